@@ -1,0 +1,25 @@
+"""Seeded synthetic inputs for blind ptychography (object, probe, scan, noise).
+
+This module builds the *inputs* of a reconstruction and nothing of the method:
+no exit wave, no Fourier projection, no update rule.  Both the FP64 oracle
+(tests) and the CUDA library (tests, bench) consume what it produces, so the
+two implementations always see identical arrays.
+
+The paper's own test images, zone-plate probe and beamline data (Sec. 4.1,
+Sec. 4.4) are not available; the recipes below stand in for them with the same
+shapes: an n x n complex object with a smooth phase field, an m x m apodised
+probe with quadratic phase, a jittered raster scan and optional Poisson noise.
+"""
+from .inputs import (  # noqa: F401
+    CONFIGS,
+    Workload,
+    make_object,
+    make_probe,
+    make_scan,
+    blur_probe,
+    poisson_noise,
+    noise_percent,
+    epoch_orders,
+    perturb,
+    make_workload,
+)
