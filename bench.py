@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Throughput of the eMAGPIE hot path on GB300: scan positions per second per epoch.
+
+Workload (one "step" = one eMAGPIE epoch over all scan positions): object
+512 x 512 complex, probe 128 x 128, 900 scan positions (30 x 30 raster, step
+12 px, +-2 px jitter), Poisson noise at 1e4 photons peak, 3 multigrid levels
+with 2x averaging restriction and bilinear prolongation, minibatch 64,
+alpha 0.05.  Inputs are synthetic and seeded (``synth``); intensities are
+simulated by the library's own forward model, then Poisson-sampled on the
+host.  The L2 cache (129 MB) is flushed by writing a 256 MB buffer before
+every timed step; inputs are resident in HBM when a step starts.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead
+(the reference arm); ``--gpus N`` under torchrun runs N independent replicas.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOAD = "mg_n512_m128"
+METRIC = "scan positions/sec per eMAGPIE epoch"
+UNIT = "positions/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_traffic.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2511_01793_gb300", "csrc", f)
+                  for f in ("emg_kernels.cu", "emg_fft.cuh", "emg_internal.h")]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload_config():
+    p = synth.CONFIGS[WORKLOAD]
+    n_pos = p["side"] ** 2
+    return {
+        "workload": f"{WORKLOAD}: object {p['n']}x{p['n']} c64, probe {p['m']}x{p['m']}, "
+                    f"{n_pos} positions ({p['side']}x{p['side']} raster, step {p['step']}, "
+                    f"+-{p['jitter']} px jitter), Poisson peak {p['peak']:g}, {p['levels']} levels "
+                    f"({p['prolong']} prolongation), minibatch {p['minibatch']}, alpha {p['alpha']}",
+        "n": p["n"], "m": p["m"], "n_pos": n_pos, "minibatch": p["minibatch"],
+        "levels": p["levels"], "prolong": p["prolong"], "alpha": p["alpha"],
+        "l2": "flushed (256 MB write) before every timed step",
+    }
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def recorded_traffic():
+    """DRAM bytes per step-kernel launch from the last ncu capture, if still current."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        if t.get("kernel_hash") == kernel_hash():
+            return float(t["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+
+        sm = [num(r[1]) for r in rows]
+        mx = max(num(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ reference arm
+
+def cpu_oracle_sample(w, d, seconds: float):
+    """The FP64 oracle (as it stands) on consecutive minibatches of the workload."""
+    import oracle as O
+
+    p = w.params
+    a = np.sqrt(np.maximum(d.astype(np.float64), 0.0))
+    z = np.ones((p["n"], p["n"]), dtype=np.complex128)
+    q = O.dp_avg_scale(w.q_init_blurred, d.astype(np.float64))
+    order = synth.epoch_orders(len(w.pos), 1, p["order_seed"])[0]
+    prm = O.Params(alpha=p["alpha"], levels=p["levels"], minibatch=p["minibatch"], prolong=p["prolong"])
+    B = p["minibatch"]
+    done, b0 = 0, 0
+    t0 = time.perf_counter()
+    while b0 < len(order):
+        idx = order[b0:b0 + B]
+        z, q = O.minibatch_step(z, q, w.pos, a, idx, prm)
+        done += len(idx)
+        b0 += B
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def host_intensities(w, rank: int):
+    """Noise-free intensities from the library's forward model, Poisson-sampled on the host."""
+    import torch
+
+    import paper_2511_01793_gb300 as emg
+
+    p = w.params
+    m, N = p["m"], len(w.pos)
+    zt = torch.from_numpy(w.z_true.astype(np.complex64)).cuda()
+    qt = torch.from_numpy(w.q_true.astype(np.complex64)).cuda()
+    pt = torch.from_numpy(w.pos).cuda()
+    out = torch.empty((N, m, m), dtype=torch.float32, device="cuda")
+    emg.emg_simulate_intensity(zt.data_ptr(), p["n"], p["n"], qt.data_ptr(), m, pt.data_ptr(), N,
+                               out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    d_clean = out.cpu().numpy().astype(np.float64)
+    rng = np.random.Generator(np.random.PCG64(p["noise_seed"] + rank))
+    return synth.poisson_noise(d_clean, p["peak"], rng).astype(np.float32)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    w = synth.make_workload(WORKLOAD)
+    import oracle as O
+
+    d = O.forward_intensity(w.q_true, w.z_true, w.pos)
+    rng = np.random.Generator(np.random.PCG64(w.params["noise_seed"]))
+    d = synth.poisson_noise(d, w.params["peak"], rng).astype(np.float32)
+    per_step = []
+    B = w.params["minibatch"]
+    for i in range(args.warmup + args.steps):
+        rate, done, dt = cpu_oracle_sample(w, d, seconds=0.0)   # exactly one minibatch
+        if i >= args.warmup:
+            per_step.append((done, dt))
+    tot_pos = sum(x[0] for x in per_step)
+    tot_t = sum(x[1] for x in per_step)
+    value = tot_pos / tot_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one minibatch of {B} positions per step from the initial state"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args, world, rank, local):
+    import torch
+
+    import paper_2511_01793_gb300 as emg
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    emg.build()
+    emg.load()
+    w = synth.make_workload(WORKLOAD)
+    p = w.params
+    m, N, B = p["m"], len(w.pos), p["minibatch"]
+    d = host_intensities(w, rank)
+    params = emg.emg_default_params(alpha=p["alpha"], levels=p["levels"], minibatch=B,
+                                    prolong=emg.EMG_PROLONG_BILINEAR if p["prolong"] == "bilinear"
+                                    else emg.EMG_PROLONG_CONST, seed=p["order_seed"] + rank)
+    z0 = np.ones((p["n"], p["n"]), dtype=np.complex64)
+    q0 = w.q_init_blurred.astype(np.complex64)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = emg.Context(w.pos, d, p["n"], p["n"], params, obj=torch.from_numpy(z0),
+                          probe=torch.from_numpy(q0), stream=stream)
+        emg.emg_normalize_probe(ctx.ctx)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+        def barrier():
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+        for _ in range(args.warmup):
+            emg.emg_run_epochs(ctx.ctx, 1)
+        emg.emg_set_profiling(ctx.ctx, True)
+        emg.emg_profile_read(ctx.ctx)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        barrier()
+        clocks.start()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            emg.emg_run_epochs(ctx.ctx, 1)
+            ev[i][1].record(stream)
+        barrier()
+        clk = clocks.stop()
+        prof = emg.emg_profile_read(ctx.ctx)
+        emg.emg_set_profiling(ctx.ctx, False)
+        total_ms = sum(a.elapsed_time(b) for a, b in ev)
+        if world > 1:
+            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        value = world * N * args.steps / (total_ms / 1e3)
+        phi_end = emg.emg_misfit(ctx.ctx)
+
+        # end-to-end through the host-buffer entry point (pinned host memory)
+        e2e = None
+        if not args.no_e2e:
+            d_pin = torch.from_numpy(d).pin_memory()
+            z_pin = torch.from_numpy(z0.copy()).pin_memory()
+            q_pin = torch.empty((m, m), dtype=torch.complex64).pin_memory()
+            q_pin.copy_(ctx.probe.cpu())
+            dn, zn, qn = d_pin.numpy(), z_pin.numpy(), q_pin.numpy()
+            for _ in range(max(1, args.warmup // 2)):
+                emg.emg_reconstruct_host(ctx.ctx, dn, zn, qn, 1, running=True)
+            t_e2e = 0.0
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                emg.emg_reconstruct_host(ctx.ctx, dn, zn, qn, 1, running=True)
+                t_e2e += time.perf_counter() - t0
+            if world > 1:
+                t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                t_e2e = float(t.item())
+            e2e = {"value": world * N * args.steps / t_e2e, "unit": UNIT,
+                   "h2d_bytes_per_step": int(d.nbytes + zn.nbytes + qn.nbytes),
+                   "d2h_bytes_per_step": int(zn.nbytes + qn.nbytes + 8)}
+
+    # roofline of the dominant kernel (the fused per-position step)
+    step_ms, step_launches = prof["step"]
+    launches_total = sum(v[1] for v in prof.values())
+    alg_bytes_per_pos = 20 * m * m             # patch read 8m^2 + amplitude 4m^2 + patch write 8m^2
+    pos_per_launch = N * args.steps / max(step_launches, 1)
+    avg_launch_s = step_ms / 1e3 / max(step_launches, 1)
+    achieved = alg_bytes_per_pos * pos_per_launch / avg_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = recorded_traffic()
+    kernel_share = {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4) for k, v in prof.items()}
+    roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 5), "peak_source": peak_kind,
+                "traffic": traffic, "kernel": "k_step<128>",
+                "algorithmic_bytes_per_launch": int(alg_bytes_per_pos * pos_per_launch),
+                "avg_launch_us": round(avg_launch_s * 1e6, 3), "launch_share": kernel_share}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(), parallelism=f"replicas{world}" if world > 1 else "single"),
+        "e2e": e2e, "gpu_launches": launches_total, "roofline": roofline, "clocks": clk,
+        "misfit_end": phi_end,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        rate, done, dt = cpu_oracle_sample(w, d, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{done} positions ({math.ceil(done / B)} minibatches of "
+                                          f"{B}) from the initial state, {dt:.1f} s single-thread FP64"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_gpu(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,245 @@
+/*
+ * emagpie.h - C ABI of the GB300 (sm_103a) eMAGPIE hot path.
+ *
+ * eMAGPIE (arXiv 2511.01793) jointly reconstructs a complex object z
+ * (n_rows x n_cols) and a complex probe Q (m x m) from far-field intensities
+ * d_k = |F(Q . P_k z)|^2 + noise, k = 0..N-1 (Sec. 2.1).  One epoch visits a
+ * random permutation of the scan positions (Sec. 3, stochastic sweep) in
+ * minibatches of B positions.  For each position k of a minibatch the library:
+ *
+ *   1. gathers z_k = P_k z (zero outside the object) and forms psi = Q . z_k;
+ *   2. takes Psi = F psi, replaces its modulus by a_k = sqrt(max(d_k, 0)) and
+ *      takes R_k = F^-1 of the result (Def. 2.1, revised exit wave);
+ *   3. computes the MAGPIE object step z+ with L multigrid levels (Sec. 3.2)
+ *      and the ePIE probe step Q+ (Sec. 4, Eq. qplus_proximal);
+ *   4. fuses them into the geometric-mean, phase-aligned joint step
+ *      (z~, Q~) of Eq. (geomean);
+ * then combines the B patches into the object and the B probe estimates into
+ * the probe (see emg_params.combine).  All positions of a minibatch see the
+ * same snapshot (z, Q); B = 1 is exactly the paper's sequential sweep.
+ *
+ * Conventions shared by every entry point:
+ *  - Complex arrays are complex64: interleaved (re, im) float pairs, row-major.
+ *  - F is the unnormalised forward 2-D DFT; F^-1 carries 1/m^2; DC at [0][0].
+ *  - The caller owns every pointer it passes; the library owns the scratch it
+ *    allocates in emg_create and frees it in emg_destroy.
+ *  - Calls are asynchronous on the context's stream unless they write host
+ *    memory, in which case they synchronise that stream before returning.
+ *  - No C++ exception or abort crosses this ABI.  Argument errors return
+ *    EMG_EINVAL before any device work is enqueued; CUDA errors return
+ *    EMG_ECUDA; emg_last_error() gives a message for the last failure.
+ *  - One context per stream; a context is not thread-safe.
+ */
+#ifndef EMAGPIE_H
+#define EMAGPIE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum emg_status {
+  EMG_OK = 0,
+  EMG_EINVAL = 1,   /* invalid argument (detected before any launch) */
+  EMG_ENOMEM = 2,   /* device or pinned host allocation failed */
+  EMG_ECUDA = 3,    /* a CUDA call or kernel failed */
+  EMG_ETIMEOUT = 4, /* a bounded device wait gave up */
+  EMG_ENOTSUP = 5   /* valid request that this build does not implement */
+} emg_status;
+
+enum { EMG_PROLONG_CONST = 0, EMG_PROLONG_BILINEAR = 1 };
+enum { EMG_COMBINE_WAVG = 0, EMG_COMBINE_SUM = 1 };
+enum { EMG_SCATTER_DETERMINISTIC = 0, EMG_SCATTER_ATOMIC = 1 };
+
+/* Same object as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* emg_stream_t;
+
+typedef struct emg_ctx emg_ctx; /* opaque, library-owned */
+
+/*
+ * The problem of Sec. 2.1: object size, probe size m, scan positions P_k
+ * and data d_k.
+ *  pos        device int32 [n_pos][2]: (row, col) of the top-left corner of
+ *             patch k in object pixels.  A patch may extend past the object;
+ *             P_k zero-pads (Sec. 2.1).  |row|, |col| must be < 2^24.
+ *  intensity  device float32 [n_pos][m][m]: d_k with DC at [0][0].  Negative
+ *             values are clamped to 0 before the square root.  Read only
+ *             during emg_create (the library keeps sqrt(d) in its own layout).
+ *  m          16, 32, 64 or 128.
+ */
+typedef struct emg_problem {
+  int32_t n_rows, n_cols;
+  int32_t m;
+  int32_t n_pos;
+  const int32_t* pos;
+  const float* intensity;
+} emg_problem;
+
+/*
+ * Hyper-parameters (Sec. 3, 3.2 and 4).
+ *  alpha      rPIE constant of the object weight u_Q = alpha (max|Q|^2 - |Q|^2), > 0.
+ *  levels     multigrid levels L >= 1 of the MAGPIE object step; m / 2^(L-1) >= 2.
+ *             L = 2 is the paper's pair of levels; L > 2 applies it recursively.
+ *  minibatch  positions per minibatch B >= 1 (1 = the paper's sequential sweep).
+ *  prolong    EMG_PROLONG_CONST: I_H^h = 4 (I_h^H)^T, piecewise-constant (paper);
+ *             EMG_PROLONG_BILINEAR: cell-centred bilinear, edge-clamped.
+ *             Restriction I_h^H is always the 2x2 average.
+ *  combine    EMG_COMBINE_WAVG: covered object pixels become
+ *               sum_k w_k z~_k / sum_k w_k, w_k(p) = |Q(p - o_k)|^2 + w_eps max|Q|^2,
+ *             and the probe the mean of Q~_k over positions with max|z_k| > 0;
+ *             EMG_COMBINE_SUM: z += sum_k (z~_k - z_k), Q += sum_k (Q~_k - Q).
+ *  scatter    EMG_SCATTER_DETERMINISTIC (bitwise repeatable; only mode built).
+ *  joint      1: geometric-mean joint step (eMAGPIE); 0: take z+ and Q+ as they
+ *             are (the rPIE-style simultaneous update of Sec. 2.2).
+ *  w_eps      weight floor of the object combine, relative to max|Q|^2, >= 0.
+ *  seed       schedule seed used when emg_run_epochs gets no order array.
+ */
+typedef struct emg_params {
+  float alpha;
+  int32_t levels;
+  int32_t minibatch;
+  int32_t prolong;
+  int32_t combine;
+  int32_t scatter;
+  int32_t joint;
+  float w_eps;
+  uint64_t seed;
+} emg_params;
+
+/* Fills *p with alpha 0.01, L 1, B 1, CONST, WAVG, DETERMINISTIC, joint 1, w_eps 1e-6, seed 0. */
+emg_status emg_default_params(emg_params* p);
+
+/* Human-readable name of a status code (static string). */
+const char* emg_status_string(emg_status s);
+
+/*
+ * Creates a context bound to `stream` on the current CUDA device, validates
+ * the problem and parameters, allocates the scratch (sqrt-intensities in the
+ * FFT's storage order, per-minibatch patch buffers, multigrid level arrays)
+ * and derives a_k = sqrt(max(d_k, 0)) from problem->intensity.
+ * On failure *out is NULL and nothing stays allocated.
+ */
+emg_status emg_create(emg_ctx** out, const emg_problem* problem,
+                      const emg_params* params, emg_stream_t stream);
+
+/*
+ * Replaces the data d_k (same shape as at creation).  `intensity` may be a
+ * device pointer or a host pointer (pinned host memory copies asynchronously;
+ * pageable memory is staged synchronously).
+ */
+emg_status emg_set_intensity(emg_ctx* ctx, const float* intensity);
+
+/*
+ * Binds the caller-owned state: object = device complex64 [n_rows][n_cols],
+ * probe = device complex64 [m][m].  Both are updated in place by the step
+ * entry points.  Fails with EMG_EINVAL for a NULL pointer.
+ */
+emg_status emg_bind_state(emg_ctx* ctx, float* object, float* probe);
+
+/*
+ * Scales the bound probe to the data, Q <- Q dp_avg / ||Q||_2 with
+ * dp_avg = sqrt(sum_ij mean_k d_k[i][j]) / m (Sec. 4.1).
+ */
+emg_status emg_normalize_probe(emg_ctx* ctx);
+
+/*
+ * One minibatch: positions idx[0..b-1] (host int32, each in [0, n_pos)),
+ * 1 <= b <= params.minibatch.  Updates the bound object and probe.
+ * If sampled_misfit (host) is not NULL it receives sum_k Phi_k at the
+ * snapshot, Phi_k = 1/2 ||Q . z_k - R_k||^2 (Eq. exit_misfit), and the call
+ * synchronises.
+ */
+emg_status emg_step_minibatch(emg_ctx* ctx, const int32_t* idx, int32_t b,
+                              double* sampled_misfit);
+
+/*
+ * Per-position diagnostics of the last emg_step_minibatch, copied to host
+ * out[b][3] = { Phi_k at the snapshot, Phi~_k(Q~, z~_k) after the joint step
+ * (the sampled surrogate of Eq. quadratic_surrogate, Prop. 3.2), max|z_k|^2 }.
+ * Phi~ after is NaN unless emg_set_verify(ctx, 1) was called.  Synchronises.
+ */
+emg_status emg_position_stats(emg_ctx* ctx, double* out, int32_t b);
+
+/* verify = 1 makes the step kernel also evaluate Phi~_k after the joint step. */
+emg_status emg_set_verify(emg_ctx* ctx, int32_t verify);
+
+/*
+ * Runs n_epochs epochs.  order: host int32 [n_epochs][n_pos], each row a
+ * permutation of 0..n_pos-1, or NULL to draw the permutation of epoch e from
+ * emg_schedule_permutation(params.seed, e, n_pos) where e counts the epochs
+ * this context has run (see emg_set_epoch).  Each epoch is cut into
+ * consecutive minibatches of params.minibatch positions (the last may be
+ * shorter).  running_misfit (host [n_epochs] or NULL) receives the sum over
+ * the epoch of the sampled Phi_k; misfit (host [n_epochs] or NULL) receives
+ * Phi(Q, z) at the end of each epoch from a separate forward pass.  The call
+ * synchronises iff it writes host output.
+ */
+emg_status emg_run_epochs(emg_ctx* ctx, int32_t n_epochs, const int32_t* order,
+                          double* running_misfit, double* misfit);
+
+/* Phi(Q, z) = 1/2 sum_k ||Q . P_k z - R_k||^2 of the bound state (host *out; synchronises). */
+emg_status emg_misfit(emg_ctx* ctx, double* out);
+
+/* Sets the epoch counter used by the default schedule (checkpoint / resume). */
+emg_status emg_set_epoch(emg_ctx* ctx, int64_t epoch);
+
+/*
+ * Host-only: the default schedule's permutation of 0..n-1 for one epoch.
+ * SplitMix64 (Steele, Lea, Flood 2014) seeded with
+ * seed + epoch * 0x9E3779B97F4A7C15 (mod 2^64), then Fisher-Yates from
+ * i = n-1 down to 1 swapping i with (next() mod (i + 1)).  out: host [n].
+ */
+emg_status emg_schedule_permutation(uint64_t seed, int64_t epoch, int32_t n, int32_t* out);
+
+/*
+ * End-to-end call on host buffers: copies intensity (host [n_pos][m][m]),
+ * object (host complex64 [n_rows][n_cols]) and probe (host complex64 [m][m])
+ * to library-owned device buffers, runs n_epochs as emg_run_epochs does and
+ * copies object and probe back.  The context's bound device state is not
+ * touched.  Synchronises.
+ */
+emg_status emg_reconstruct_host(emg_ctx* ctx, const float* intensity, float* object,
+                                float* probe, int32_t n_epochs, const int32_t* order,
+                                double* running_misfit, double* misfit);
+
+/*
+ * Forward model of Sec. 2.1 without a context: d_k = |F(Q . P_k z)|^2 for
+ * k = 0..n_pos-1.  object device complex64 [n_rows][n_cols], probe device
+ * complex64 [m][m], pos device int32 [n_pos][2], out device float32
+ * [n_pos][m][m] (DC at [0][0]).  Asynchronous on `stream`.
+ */
+emg_status emg_simulate_intensity(const float* object, int32_t n_rows, int32_t n_cols,
+                                  const float* probe, int32_t m, const int32_t* pos,
+                                  int32_t n_pos, float* out, emg_stream_t stream);
+
+/*
+ * Batched 2-D DFT of count m x m complex64 tiles (device, natural order in
+ * and out): inverse = 0 gives F x (unnormalised), inverse = 1 gives F^-1 x
+ * (with 1/m^2).  in and out may alias.  Asynchronous on `stream`.
+ */
+emg_status emg_fft2(const float* in, float* out, int32_t m, int32_t count, int32_t inverse,
+                    emg_stream_t stream);
+
+/*
+ * Kernel timing for measurement (not part of the method).  enable = 1 makes
+ * every later launch of the minibatch path record a pair of CUDA events on the
+ * context's stream.  emg_profile_read synchronises and returns, per kernel
+ * kind {probe prep, per-position step, combine, other}, the summed event time
+ * in milliseconds (ms[4], host) and the number of launches (launches[4], host;
+ * counted whether or not profiling is on) since the last read, then resets.
+ */
+emg_status emg_set_profiling(emg_ctx* ctx, int32_t enable);
+emg_status emg_profile_read(emg_ctx* ctx, double* ms, int64_t* launches);
+
+/* Message of the last failure on this context (static until the next call). */
+emg_status emg_last_error(const emg_ctx* ctx, const char** msg);
+
+/* Frees everything the context owns; NULL is a no-op. */
+void emg_destroy(emg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMAGPIE_H */

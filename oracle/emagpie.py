@@ -64,6 +64,8 @@ class Params:
     prolong   'const' (I_H^h = 4 (I_h^H)^T) or 'bilinear'
     combine   'wavg' (weighted mean) or 'sum' (sum of per-position corrections)
     w_eps     floor of the object-combine weight, relative to max|Q|^2
+    joint     True: geometric-mean joint step (Eq. geomean); False: take z^+ and
+              Q^+ as they are (the simultaneous rPIE update of Sec. 2.2)
     """
 
     alpha: float = 0.01
@@ -72,6 +74,7 @@ class Params:
     prolong: str = "const"
     combine: str = "wavg"
     w_eps: float = 1e-6
+    joint: bool = True
 
 
 # ---------------------------------------------------------------------------
@@ -282,7 +285,8 @@ def geometric_mean_aligned(x: np.ndarray, x_plus: np.ndarray) -> np.ndarray:
     return root
 
 
-def joint_step(Q, z_k, a_k, alpha: float, levels: int = 1, kind: str = "const"):
+def joint_step(Q, z_k, a_k, alpha: float, levels: int = 1, kind: str = "const",
+               joint: bool = True):
     """One eMAGPIE position update (Sec. 3, Sec. 3.2, Sec. 4).
 
     Returns a dict with the revised exit wave R, the one-variable minimisers
@@ -293,8 +297,11 @@ def joint_step(Q, z_k, a_k, alpha: float, levels: int = 1, kind: str = "const"):
     u = u_probe_reg(Q, alpha)
     z_plus = magpie_zplus(Q, z_k, R, u, levels, kind)
     Q_plus = probe_plus(Q, z_k, R)
-    z_t = geometric_mean_aligned(z_k, z_plus)
-    Q_t = geometric_mean_aligned(Q, Q_plus)
+    if joint:
+        z_t = geometric_mean_aligned(z_k, z_plus)
+        Q_t = geometric_mean_aligned(Q, Q_plus)
+    else:
+        z_t, Q_t = z_plus, Q_plus
     mu = float(np.max(np.abs(z_k) ** 2))
     return dict(R=R, z_plus=z_plus, Q_plus=Q_plus, z_t=z_t, Q_t=Q_t, mu=mu,
                 u_Q=u, u_z=u_object_reg(z_k),
@@ -327,7 +334,7 @@ def minibatch_step(z, Q, pos, a, idx, params: Params, out: Optional[dict] = None
     diag = []
     for k in idx:
         z_k = select_patch(z, pos[k], m)
-        st = joint_step(Q, z_k, a[k], params.alpha, params.levels, params.prolong)
+        st = joint_step(Q, z_k, a[k], params.alpha, params.levels, params.prolong, params.joint)
         diag.append(st)
         w = absQ2 + params.w_eps * M_Q
         obj, pat = _patch_slices(z.shape, pos[k], m)
@@ -386,7 +393,7 @@ def sequential_sweep(z, Q, pos, a, order, params: Params):
     Q = Q.copy()
     for k in order:
         z_k = select_patch(z, pos[k], m)
-        st = joint_step(Q, z_k, a[k], params.alpha, params.levels, params.prolong)
+        st = joint_step(Q, z_k, a[k], params.alpha, params.levels, params.prolong, params.joint)
         obj, pat = _patch_slices(z.shape, pos[k], m)
         z[obj] = st["z_t"][pat]
         Q = st["Q_t"]

@@ -1,0 +1,717 @@
+// C ABI of the eMAGPIE hot path: context, validation, scratch ownership and
+// the minibatch / epoch drivers (Sec. 3 stochastic sweep of arXiv 2511.01793).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/emagpie.h"
+#include "emg_internal.h"
+
+using emg::ApplyArgs;
+using emg::kMaxLevels;
+using emg::PrepArgs;
+using emg::StepArgs;
+
+// Kernel kinds counted and timed by the profiling hooks.
+enum { kKindPrep = 0, kKindStep = 1, kKindApply = 2, kKindOther = 3, kKinds = 4 };
+
+struct emg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int n_rows = 0, n_cols = 0, m = 0, n_pos = 0;
+  emg_params par{};
+  int verify = 0;
+  int64_t epoch = 0;
+  std::string err;
+  int last_b = 0;
+
+  // caller-bound state
+  float2* object = nullptr;
+  float2* probe = nullptr;
+
+  // library-owned device buffers
+  int32_t* d_pos = nullptr;       // [N][2]
+  float* d_amp = nullptr;         // [N][m][m] storage order
+  float2* d_zt = nullptr;         // [B][m][m]
+  float2* d_qt = nullptr;         // [B][m][m]
+  float* d_mu = nullptr;          // [B]
+  double* d_phi = nullptr;        // [N]
+  double* d_phi_after = nullptr;  // [B]
+  double* d_partial = nullptr;    // [N] misfit partials
+  double* d_scalar = nullptr;     // [64] assorted scalar results
+  double* d_norm = nullptr;       // [1024] normalisation partials
+  float* d_wq = nullptr;          // [m][m]
+  void* d_levels = nullptr;       // all multigrid arrays
+  int32_t* d_orders = nullptr;    // [cap_orders]
+  size_t cap_orders = 0;
+  double* d_hist = nullptr;       // [2][cap_hist]
+  size_t cap_hist = 0;
+  float* d_stage_d = nullptr;     // [N][m][m] intensity staging (host input path)
+  float2* d_own_object = nullptr; // host-buffer path state
+  float2* d_own_probe = nullptr;
+  double* h_scalar = nullptr;     // pinned [64]
+
+  // kernel timing (emg_set_profiling): CUDA events around each launch, per kernel kind
+  int profile = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;
+  size_t ev_used = 0;
+  int64_t launches[kKinds] = {0, 0, 0, 0};
+
+  std::vector<int32_t> h_pos;
+  PrepArgs prep{};
+  emg::LevelArrays lv{};
+};
+
+namespace {
+
+std::mutex g_init_mu;
+bool g_init_done[256] = {false};
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+emg_status fail(emg_ctx* c, emg_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+emg_status cuda_fail(emg_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, EMG_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define EMG_CUDA(ctx, call)                                   \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+  } while (0)
+
+// Brackets one launch with a pair of events on the context's stream when profiling.
+struct LaunchMark {
+  emg_ctx* c;
+  int kind;
+  cudaEvent_t stop = nullptr;
+  LaunchMark(emg_ctx* ctx, int k) : c(ctx), kind(k) {
+    c->launches[k] += 1;
+    if (!c->profile) return;
+    if (c->ev_used + 2 > c->ev_pool.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        c->ev_pool.push_back(e);
+      }
+    }
+    cudaEvent_t start = c->ev_pool[c->ev_used++];
+    stop = c->ev_pool[c->ev_used++];
+    cudaEventRecord(start, c->stream);
+    c->ev_marks.push_back({k, {start, stop}});
+  }
+  ~LaunchMark() {
+    if (stop) cudaEventRecord(stop, c->stream);
+  }
+};
+
+cudaError_t ensure_device_init(int dev) {
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  if (g_init_done[dev]) return cudaSuccess;
+  cudaError_t e = emg::upload_twiddles();
+  if (e == cudaSuccess) g_init_done[dev] = true;
+  return e;
+}
+
+bool valid_m(int m) { return m == 16 || m == 32 || m == 64 || m == 128; }
+
+emg_status validate_params(emg_ctx* c, const emg_params* p, int m, int n_pos) {
+  if (!p) return fail(c, EMG_EINVAL, "params is NULL");
+  if (!(p->alpha > 0.f) || !isfinite(p->alpha)) return fail(c, EMG_EINVAL, "alpha must be finite and > 0");
+  if (p->levels < 1 || p->levels > kMaxLevels) return fail(c, EMG_EINVAL, "levels out of range [1, 7]");
+  if ((m >> (p->levels - 1)) < 2) return fail(c, EMG_EINVAL, "m / 2^(levels-1) must be >= 2");
+  if (p->minibatch < 1 || p->minibatch > 4096 || p->minibatch > n_pos)
+    return fail(c, EMG_EINVAL, "minibatch must be in [1, min(n_pos, 4096)]");
+  if (p->prolong != EMG_PROLONG_CONST && p->prolong != EMG_PROLONG_BILINEAR)
+    return fail(c, EMG_EINVAL, "prolong must be EMG_PROLONG_CONST or EMG_PROLONG_BILINEAR");
+  if (p->combine != EMG_COMBINE_WAVG && p->combine != EMG_COMBINE_SUM)
+    return fail(c, EMG_EINVAL, "combine must be EMG_COMBINE_WAVG or EMG_COMBINE_SUM");
+  if (p->scatter == EMG_SCATTER_ATOMIC) return fail(c, EMG_ENOTSUP, "EMG_SCATTER_ATOMIC is not built");
+  if (p->scatter != EMG_SCATTER_DETERMINISTIC) return fail(c, EMG_EINVAL, "unknown scatter mode");
+  if (p->joint != 0 && p->joint != 1) return fail(c, EMG_EINVAL, "joint must be 0 or 1");
+  if (!(p->w_eps >= 0.f) || !isfinite(p->w_eps)) return fail(c, EMG_EINVAL, "w_eps must be finite and >= 0");
+  if (emg::step_smem_bytes(m, p->levels) > (size_t)emg::step_smem_limit())
+    return fail(c, EMG_ENOTSUP, "too many levels for the shared-memory budget of this m");
+  return EMG_OK;
+}
+
+template <typename T>
+cudaError_t dmalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+void free_all(emg_ctx* c) {
+  cudaFree(c->d_pos);
+  cudaFree(c->d_amp);
+  cudaFree(c->d_zt);
+  cudaFree(c->d_qt);
+  cudaFree(c->d_mu);
+  cudaFree(c->d_phi);
+  cudaFree(c->d_phi_after);
+  cudaFree(c->d_partial);
+  cudaFree(c->d_scalar);
+  cudaFree(c->d_norm);
+  cudaFree(c->d_wq);
+  cudaFree(c->d_levels);
+  cudaFree(c->d_orders);
+  cudaFree(c->d_hist);
+  cudaFree(c->d_stage_d);
+  cudaFree(c->d_own_object);
+  cudaFree(c->d_own_probe);
+  if (c->h_scalar) cudaFreeHost(c->h_scalar);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  c->ev_pool.clear();
+}
+
+// Carves the multigrid level arrays out of one allocation.
+emg_status alloc_levels(emg_ctx* c) {
+  const int m = c->m, L = c->par.levels;
+  size_t bytes = 0;
+  auto take = [&](size_t b) {
+    size_t off = (bytes + 255) & ~(size_t)255;
+    bytes = off + b;
+    return off;
+  };
+  size_t offG[kMaxLevels], offQ[kMaxLevels], offWz[kMaxLevels], offWR[kMaxLevels], offU[kMaxLevels],
+      offT[kMaxLevels];
+  for (int l = 0; l < L; ++l) {
+    const size_t n = (size_t)(m >> l) * (m >> l);
+    offG[l] = take(n * sizeof(float2));
+    offQ[l] = take(n * sizeof(float2));
+    offU[l] = take(n * sizeof(float));
+    if (l + 1 < L) {
+      offWz[l] = take(n * sizeof(float));
+      offWR[l] = take(n * sizeof(float2));
+      offT[l] = take(n / 4 * sizeof(float));
+    }
+  }
+  cudaError_t e = cudaMalloc(&c->d_levels, bytes);
+  if (e != cudaSuccess) return fail(c, EMG_ENOMEM, "cudaMalloc(levels) failed");
+  char* base = (char*)c->d_levels;
+  PrepArgs& pa = c->prep;
+  memset(&pa, 0, sizeof(pa));
+  memset(&c->lv, 0, sizeof(c->lv));
+  for (int l = 0; l < L; ++l) {
+    pa.G[l] = (float2*)(base + offG[l]);
+    pa.Q[l] = (float2*)(base + offQ[l]);
+    pa.u[l] = (float*)(base + offU[l]);
+    c->lv.G[l] = pa.G[l];
+    c->lv.Q[l] = pa.Q[l];
+    if (l + 1 < L) {
+      pa.Wz[l] = (float*)(base + offWz[l]);
+      pa.WR[l] = (float2*)(base + offWR[l]);
+      pa.T[l] = (float*)(base + offT[l]);
+      c->lv.Wz[l] = pa.Wz[l];
+      c->lv.WR[l] = pa.WR[l];
+    }
+  }
+  pa.m = m;
+  pa.levels = L;
+  pa.prolong = c->par.prolong;
+  pa.alpha = c->par.alpha;
+  pa.w_eps = c->par.w_eps;
+  pa.wq = c->d_wq;
+  return EMG_OK;
+}
+
+emg_status ensure_orders(emg_ctx* c, size_t n) {
+  if (n <= c->cap_orders) return EMG_OK;
+  cudaFree(c->d_orders);
+  c->d_orders = nullptr;
+  c->cap_orders = 0;
+  if (cudaMalloc(&c->d_orders, n * sizeof(int32_t)) != cudaSuccess)
+    return fail(c, EMG_ENOMEM, "cudaMalloc(orders) failed");
+  c->cap_orders = n;
+  return EMG_OK;
+}
+
+emg_status ensure_hist(emg_ctx* c, size_t n) {
+  if (n <= c->cap_hist) return EMG_OK;
+  cudaFree(c->d_hist);
+  c->d_hist = nullptr;
+  c->cap_hist = 0;
+  if (cudaMalloc(&c->d_hist, 2 * n * sizeof(double)) != cudaSuccess)
+    return fail(c, EMG_ENOMEM, "cudaMalloc(history) failed");
+  c->cap_hist = n;
+  return EMG_OK;
+}
+
+uint64_t splitmix_next(uint64_t& s) {
+  s += 0x9E3779B97F4A7C15ull;
+  uint64_t x = s;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+void permutation(uint64_t seed, int64_t epoch, int32_t n, int32_t* out) {
+  uint64_t s = seed + (uint64_t)epoch * 0x9E3779B97F4A7C15ull;
+  for (int32_t i = 0; i < n; ++i) out[i] = i;
+  for (int32_t i = n - 1; i >= 1; --i) {
+    const uint64_t j = splitmix_next(s) % (uint64_t)(i + 1);
+    const int32_t t = out[i];
+    out[i] = out[j];
+    out[j] = t;
+  }
+}
+
+// Enqueues one minibatch: probe prep, per-position step, combine.
+emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_phi_out) {
+  if (!c->object || !c->probe) return fail(c, EMG_EINVAL, "no state bound");
+  PrepArgs pa = c->prep;
+  pa.probe = c->probe;  // the probe bound right now (emg_reconstruct_host swaps it)
+  cudaError_t e;
+  {
+    LaunchMark mk(c, kKindPrep);
+    e = emg::launch_prep(pa, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_prep launch");
+  StepArgs sa{};
+  sa.object = c->object;
+  sa.probe = c->probe;
+  sa.pos = c->d_pos;
+  sa.amp = c->d_amp;
+  sa.order = d_idx;
+  sa.n_rows = c->n_rows;
+  sa.n_cols = c->n_cols;
+  sa.levels = c->par.levels;
+  sa.prolong = c->par.prolong;
+  sa.joint = c->par.joint;
+  sa.verify = c->verify;
+  sa.lv = c->lv;
+  sa.zt = c->d_zt;
+  sa.qt = c->d_qt;
+  sa.mu = c->d_mu;
+  sa.phi = d_phi_out;
+  sa.phi_after = c->d_phi_after;
+  {
+    LaunchMark mk(c, kKindStep);
+    e = emg::launch_step(c->m, b, sa, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_step launch");
+  ApplyArgs aa{};
+  aa.object = c->object;
+  aa.probe = c->probe;
+  aa.pos = c->d_pos;
+  aa.order = d_idx;
+  aa.b = b;
+  aa.n_rows = c->n_rows;
+  aa.n_cols = c->n_cols;
+  aa.m = c->m;
+  aa.combine = c->par.combine;
+  aa.zt = c->d_zt;
+  aa.qt = c->d_qt;
+  aa.mu = c->d_mu;
+  aa.wq = c->d_wq;
+  aa.tiles_x = (c->n_cols + emg::kApplyTile - 1) / emg::kApplyTile;
+  aa.tiles_y = (c->n_rows + emg::kApplyTile - 1) / emg::kApplyTile;
+  {
+    LaunchMark mk(c, kKindApply);
+    e = emg::launch_apply(aa, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_apply launch");
+  return EMG_OK;
+}
+
+emg_status check_bound(emg_ctx* c) {
+  if (!c->object || !c->probe) return fail(c, EMG_EINVAL, "no state bound (call emg_bind_state)");
+  return EMG_OK;
+}
+
+emg_status run_epochs_impl(emg_ctx* c, int32_t n_epochs, const int32_t* order, double* running,
+                           double* misfit) {
+  if (n_epochs < 0) return fail(c, EMG_EINVAL, "n_epochs < 0");
+  if (n_epochs == 0) return EMG_OK;
+  const int N = c->n_pos, B = c->par.minibatch;
+  std::vector<int32_t> h((size_t)n_epochs * N);
+  if (order) {
+    std::vector<unsigned char> seen(N);
+    for (int32_t e = 0; e < n_epochs; ++e) {
+      std::fill(seen.begin(), seen.end(), 0);
+      for (int i = 0; i < N; ++i) {
+        const int32_t v = order[(size_t)e * N + i];
+        if (v < 0 || v >= N || seen[v]) return fail(c, EMG_EINVAL, "order row is not a permutation of 0..n_pos-1");
+        seen[v] = 1;
+      }
+    }
+    memcpy(h.data(), order, h.size() * sizeof(int32_t));
+  } else {
+    for (int32_t e = 0; e < n_epochs; ++e) permutation(c->par.seed, c->epoch + e, N, h.data() + (size_t)e * N);
+  }
+  emg_status st = ensure_orders(c, h.size());
+  if (st != EMG_OK) return st;
+  if ((st = ensure_hist(c, n_epochs)) != EMG_OK) return st;
+  EMG_CUDA(c, cudaMemcpyAsync(c->d_orders, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  for (int32_t e = 0; e < n_epochs; ++e) {
+    const int32_t* ord = c->d_orders + (size_t)e * N;
+    for (int b0 = 0; b0 < N; b0 += B) {
+      const int b = (N - b0 < B) ? N - b0 : B;
+      if ((st = enqueue_minibatch(c, ord + b0, b, c->d_phi + b0)) != EMG_OK) return st;
+    }
+    if (running) {
+      c->launches[kKindOther] += 1;
+      cudaError_t ce = emg::launch_sum(c->d_phi, N, 1.0, c->d_hist + e, c->stream);
+      if (ce != cudaSuccess) return cuda_fail(c, ce, "k_sum launch");
+    }
+    if (misfit) {
+      c->launches[kKindOther] += 2;
+      cudaError_t ce = emg::launch_misfit(c->m, c->object, c->probe, c->d_pos, c->d_amp, c->n_rows,
+                                          c->n_cols, N, c->d_partial, c->stream);
+      if (ce != cudaSuccess) return cuda_fail(c, ce, "k_misfit launch");
+      ce = emg::launch_sum(c->d_partial, N, 1.0, c->d_hist + c->cap_hist + e, c->stream);
+      if (ce != cudaSuccess) return cuda_fail(c, ce, "k_sum launch");
+    }
+  }
+  c->epoch += n_epochs;
+  if (running)
+    EMG_CUDA(c, cudaMemcpyAsync(running, c->d_hist, n_epochs * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (misfit)
+    EMG_CUDA(c, cudaMemcpyAsync(misfit, c->d_hist + c->cap_hist, n_epochs * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+  if (running || misfit) EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  else EMG_CUDA(c, cudaGetLastError());
+  return EMG_OK;
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+emg_status set_intensity_impl(emg_ctx* c, const float* intensity) {
+  const size_t n = (size_t)c->n_pos * c->m * c->m;
+  const float* src = intensity;
+  if (!is_device_pointer(intensity)) {
+    if (!c->d_stage_d && cudaMalloc(&c->d_stage_d, n * sizeof(float)) != cudaSuccess)
+      return fail(c, EMG_ENOMEM, "cudaMalloc(intensity staging) failed");
+    EMG_CUDA(c, cudaMemcpyAsync(c->d_stage_d, intensity, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    src = c->d_stage_d;
+  }
+  cudaError_t e = emg::launch_amp_prep(src, c->d_amp, c->m, c->n_pos, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_amp_prep launch");
+  return EMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+emg_status emg_default_params(emg_params* p) {
+  if (!p) return EMG_EINVAL;
+  p->alpha = 0.01f;
+  p->levels = 1;
+  p->minibatch = 1;
+  p->prolong = EMG_PROLONG_CONST;
+  p->combine = EMG_COMBINE_WAVG;
+  p->scatter = EMG_SCATTER_DETERMINISTIC;
+  p->joint = 1;
+  p->w_eps = 1e-6f;
+  p->seed = 0;
+  return EMG_OK;
+}
+
+const char* emg_status_string(emg_status s) {
+  switch (s) {
+    case EMG_OK: return "EMG_OK";
+    case EMG_EINVAL: return "EMG_EINVAL";
+    case EMG_ENOMEM: return "EMG_ENOMEM";
+    case EMG_ECUDA: return "EMG_ECUDA";
+    case EMG_ETIMEOUT: return "EMG_ETIMEOUT";
+    case EMG_ENOTSUP: return "EMG_ENOTSUP";
+  }
+  return "EMG_UNKNOWN";
+}
+
+emg_status emg_create(emg_ctx** out, const emg_problem* pr, const emg_params* par, emg_stream_t stream) {
+  if (!out) return EMG_EINVAL;
+  *out = nullptr;
+  if (!pr || !par) return EMG_EINVAL;
+  if (pr->n_rows < 1 || pr->n_cols < 1 || pr->n_pos < 1 || !pr->pos || !pr->intensity) return EMG_EINVAL;
+  if (!valid_m(pr->m)) return EMG_ENOTSUP;
+  if ((int64_t)pr->n_rows * pr->n_cols > ((int64_t)1 << 34)) return EMG_EINVAL;
+  emg_ctx* c = new (std::nothrow) emg_ctx();
+  if (!c) return EMG_ENOMEM;
+  emg_status st = validate_params(c, par, pr->m, pr->n_pos);
+  if (st != EMG_OK) {
+    delete c;
+    return st;
+  }
+  c->n_rows = pr->n_rows;
+  c->n_cols = pr->n_cols;
+  c->m = pr->m;
+  c->n_pos = pr->n_pos;
+  c->par = *par;
+  c->stream = (cudaStream_t)stream;
+  auto bail = [&](emg_status s) {
+    free_all(c);
+    delete c;
+    return s;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) return bail(EMG_ECUDA);
+  if (ensure_device_init(c->device) != cudaSuccess) return bail(EMG_ECUDA);
+  const int N = c->n_pos, m = c->m, B = par->minibatch;
+  const size_t mm = (size_t)m * m;
+  if (dmalloc(&c->d_pos, (size_t)2 * N) || dmalloc(&c->d_amp, (size_t)N * mm) ||
+      dmalloc(&c->d_zt, (size_t)B * mm) || dmalloc(&c->d_qt, (size_t)B * mm) ||
+      dmalloc(&c->d_mu, (size_t)B) || dmalloc(&c->d_phi, (size_t)N) ||
+      dmalloc(&c->d_phi_after, (size_t)B) || dmalloc(&c->d_partial, (size_t)N) ||
+      dmalloc(&c->d_scalar, (size_t)64) || dmalloc(&c->d_norm, (size_t)1024) ||
+      dmalloc(&c->d_wq, mm))
+    return bail(EMG_ENOMEM);
+  if (cudaMallocHost(&c->h_scalar, 64 * sizeof(double)) != cudaSuccess) return bail(EMG_ENOMEM);
+  if (alloc_levels(c) != EMG_OK) return bail(EMG_ENOMEM);
+  c->h_pos.resize((size_t)2 * N);
+  if (cudaMemcpyAsync(c->h_pos.data(), pr->pos, c->h_pos.size() * sizeof(int32_t), cudaMemcpyDefault,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return bail(EMG_ECUDA);
+  for (int32_t v : c->h_pos)
+    if (v <= -(1 << 24) || v >= (1 << 24)) return bail(EMG_EINVAL);
+  if (cudaMemcpyAsync(c->d_pos, c->h_pos.data(), c->h_pos.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess)
+    return bail(EMG_ECUDA);
+  if (cudaMemsetAsync(c->d_phi_after, 0xff, (size_t)B * sizeof(double), c->stream) != cudaSuccess)
+    return bail(EMG_ECUDA);
+  if (set_intensity_impl(c, pr->intensity) != EMG_OK) return bail(EMG_ECUDA);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(EMG_ECUDA);
+  *out = c;
+  return EMG_OK;
+}
+
+emg_status emg_set_intensity(emg_ctx* c, const float* intensity) {
+  if (!c) return EMG_EINVAL;
+  if (!intensity) return fail(c, EMG_EINVAL, "intensity is NULL");
+  DeviceGuard g(c->device);
+  return set_intensity_impl(c, intensity);
+}
+
+emg_status emg_bind_state(emg_ctx* c, float* object, float* probe) {
+  if (!c) return EMG_EINVAL;
+  if (!object || !probe) return fail(c, EMG_EINVAL, "object or probe is NULL");
+  c->object = (float2*)object;
+  c->probe = (float2*)probe;
+  return EMG_OK;
+}
+
+emg_status emg_normalize_probe(emg_ctx* c) {
+  if (!c) return EMG_EINVAL;
+  emg_status st = check_bound(c);
+  if (st != EMG_OK) return st;
+  DeviceGuard g(c->device);
+  cudaError_t e = emg::launch_normalize_probe(c->d_amp, c->m, c->n_pos, c->probe, c->d_norm, 1024, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "normalize launch");
+  return EMG_OK;
+}
+
+emg_status emg_step_minibatch(emg_ctx* c, const int32_t* idx, int32_t b, double* sampled_misfit) {
+  if (!c) return EMG_EINVAL;
+  emg_status st = check_bound(c);
+  if (st != EMG_OK) return st;
+  if (!idx) return fail(c, EMG_EINVAL, "idx is NULL");
+  if (b < 1 || b > c->par.minibatch) return fail(c, EMG_EINVAL, "b must be in [1, params.minibatch]");
+  for (int i = 0; i < b; ++i)
+    if (idx[i] < 0 || idx[i] >= c->n_pos) return fail(c, EMG_EINVAL, "idx entry out of range");
+  DeviceGuard g(c->device);
+  if ((st = ensure_orders(c, (size_t)c->n_pos)) != EMG_OK) return st;
+  EMG_CUDA(c, cudaMemcpyAsync(c->d_orders, idx, (size_t)b * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  if ((st = enqueue_minibatch(c, c->d_orders, b, c->d_phi)) != EMG_OK) return st;
+  c->last_b = b;
+  if (sampled_misfit) {
+    cudaError_t e = emg::launch_sum(c->d_phi, b, 1.0, c->d_scalar, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "k_sum launch");
+    EMG_CUDA(c, cudaMemcpyAsync(c->h_scalar, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+    *sampled_misfit = c->h_scalar[0];
+  }
+  return EMG_OK;
+}
+
+emg_status emg_position_stats(emg_ctx* c, double* out, int32_t b) {
+  if (!c) return EMG_EINVAL;
+  if (!out || b < 1 || b > c->last_b) return fail(c, EMG_EINVAL, "b must be in [1, last minibatch size]");
+  DeviceGuard g(c->device);
+  std::vector<double> phi(b), after(b);
+  std::vector<float> mu(b);
+  EMG_CUDA(c, cudaMemcpyAsync(phi.data(), c->d_phi, b * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  EMG_CUDA(c, cudaMemcpyAsync(after.data(), c->d_phi_after, b * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  EMG_CUDA(c, cudaMemcpyAsync(mu.data(), c->d_mu, b * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < b; ++i) {
+    out[3 * i] = phi[i];
+    out[3 * i + 1] = c->verify ? after[i] : NAN;
+    out[3 * i + 2] = mu[i];
+  }
+  return EMG_OK;
+}
+
+emg_status emg_set_verify(emg_ctx* c, int32_t verify) {
+  if (!c) return EMG_EINVAL;
+  c->verify = verify ? 1 : 0;
+  return EMG_OK;
+}
+
+emg_status emg_run_epochs(emg_ctx* c, int32_t n_epochs, const int32_t* order, double* running_misfit,
+                          double* misfit) {
+  if (!c) return EMG_EINVAL;
+  emg_status st = check_bound(c);
+  if (st != EMG_OK) return st;
+  DeviceGuard g(c->device);
+  return run_epochs_impl(c, n_epochs, order, running_misfit, misfit);
+}
+
+emg_status emg_misfit(emg_ctx* c, double* out) {
+  if (!c) return EMG_EINVAL;
+  emg_status st = check_bound(c);
+  if (st != EMG_OK) return st;
+  if (!out) return fail(c, EMG_EINVAL, "out is NULL");
+  DeviceGuard g(c->device);
+  cudaError_t e = emg::launch_misfit(c->m, c->object, c->probe, c->d_pos, c->d_amp, c->n_rows, c->n_cols,
+                                     c->n_pos, c->d_partial, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_misfit launch");
+  e = emg::launch_sum(c->d_partial, c->n_pos, 1.0, c->d_scalar, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_sum launch");
+  EMG_CUDA(c, cudaMemcpyAsync(c->h_scalar, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  *out = c->h_scalar[0];
+  return EMG_OK;
+}
+
+emg_status emg_set_epoch(emg_ctx* c, int64_t epoch) {
+  if (!c) return EMG_EINVAL;
+  if (epoch < 0) return fail(c, EMG_EINVAL, "epoch < 0");
+  c->epoch = epoch;
+  return EMG_OK;
+}
+
+emg_status emg_schedule_permutation(uint64_t seed, int64_t epoch, int32_t n, int32_t* out) {
+  if (n < 0 || (n > 0 && !out) || epoch < 0) return EMG_EINVAL;
+  permutation(seed, epoch, n, out);
+  return EMG_OK;
+}
+
+emg_status emg_reconstruct_host(emg_ctx* c, const float* intensity, float* object, float* probe,
+                                int32_t n_epochs, const int32_t* order, double* running_misfit,
+                                double* misfit) {
+  if (!c) return EMG_EINVAL;
+  if (!intensity || !object || !probe) return fail(c, EMG_EINVAL, "NULL host buffer");
+  DeviceGuard g(c->device);
+  const size_t nz = (size_t)c->n_rows * c->n_cols, nq = (size_t)c->m * c->m;
+  if (!c->d_own_object && cudaMalloc(&c->d_own_object, nz * sizeof(float2)) != cudaSuccess)
+    return fail(c, EMG_ENOMEM, "cudaMalloc(object) failed");
+  if (!c->d_own_probe && cudaMalloc(&c->d_own_probe, nq * sizeof(float2)) != cudaSuccess)
+    return fail(c, EMG_ENOMEM, "cudaMalloc(probe) failed");
+  emg_status st = set_intensity_impl(c, intensity);
+  if (st != EMG_OK) return st;
+  EMG_CUDA(c, cudaMemcpyAsync(c->d_own_object, object, nz * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
+  EMG_CUDA(c, cudaMemcpyAsync(c->d_own_probe, probe, nq * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
+  float2* keep_o = c->object;
+  float2* keep_p = c->probe;
+  c->object = c->d_own_object;
+  c->probe = c->d_own_probe;
+  st = run_epochs_impl(c, n_epochs, order, running_misfit, misfit);
+  c->object = keep_o;
+  c->probe = keep_p;
+  if (st != EMG_OK) return st;
+  EMG_CUDA(c, cudaMemcpyAsync(object, c->d_own_object, nz * sizeof(float2), cudaMemcpyDeviceToHost, c->stream));
+  EMG_CUDA(c, cudaMemcpyAsync(probe, c->d_own_probe, nq * sizeof(float2), cudaMemcpyDeviceToHost, c->stream));
+  EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return EMG_OK;
+}
+
+emg_status emg_simulate_intensity(const float* object, int32_t n_rows, int32_t n_cols, const float* probe,
+                                  int32_t m, const int32_t* pos, int32_t n_pos, float* out,
+                                  emg_stream_t stream) {
+  if (!object || !probe || !pos || !out || n_rows < 1 || n_cols < 1 || n_pos < 0) return EMG_EINVAL;
+  if (!valid_m(m)) return EMG_ENOTSUP;
+  if (n_pos == 0) return EMG_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || ensure_device_init(dev) != cudaSuccess) return EMG_ECUDA;
+  cudaError_t e = emg::launch_simulate(m, (const float2*)object, (const float2*)probe, pos, n_rows, n_cols,
+                                       n_pos, out, (cudaStream_t)stream);
+  return e == cudaSuccess ? EMG_OK : EMG_ECUDA;
+}
+
+emg_status emg_fft2(const float* in, float* out, int32_t m, int32_t count, int32_t inverse,
+                    emg_stream_t stream) {
+  if (!in || !out || count < 0 || (inverse != 0 && inverse != 1)) return EMG_EINVAL;
+  if (!valid_m(m)) return EMG_ENOTSUP;
+  if (count == 0) return EMG_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || ensure_device_init(dev) != cudaSuccess) return EMG_ECUDA;
+  cudaError_t e = emg::launch_fft2(m, (const float2*)in, (float2*)out, count, inverse, (cudaStream_t)stream);
+  return e == cudaSuccess ? EMG_OK : EMG_ECUDA;
+}
+
+emg_status emg_set_profiling(emg_ctx* c, int32_t enable) {
+  if (!c) return EMG_EINVAL;
+  c->profile = enable ? 1 : 0;
+  return EMG_OK;
+}
+
+emg_status emg_profile_read(emg_ctx* c, double* ms, int64_t* launches) {
+  if (!c) return EMG_EINVAL;
+  if (!ms || !launches) return fail(c, EMG_EINVAL, "NULL output");
+  DeviceGuard g(c->device);
+  EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  double acc[kKinds] = {0, 0, 0, 0};
+  for (auto& mk : c->ev_marks) {
+    float t = 0.f;
+    EMG_CUDA(c, cudaEventElapsedTime(&t, mk.second.first, mk.second.second));
+    acc[mk.first] += t;
+  }
+  for (int i = 0; i < kKinds; ++i) {
+    ms[i] = acc[i];
+    launches[i] = c->launches[i];
+    c->launches[i] = 0;
+  }
+  c->ev_marks.clear();
+  c->ev_used = 0;
+  return EMG_OK;
+}
+
+emg_status emg_last_error(const emg_ctx* c, const char** msg) {
+  if (!c || !msg) return EMG_EINVAL;
+  *msg = c->err.c_str();
+  return EMG_OK;
+}
+
+void emg_destroy(emg_ctx* c) {
+  if (!c) return;
+  {
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    free_all(c);
+  }
+  delete c;
+}
+
+}  // extern "C"

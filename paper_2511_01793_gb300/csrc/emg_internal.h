@@ -1,0 +1,88 @@
+// Internal interface between the C ABI layer (emg_capi.cu) and the kernels
+// (emg_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace emg {
+
+constexpr int kMaxLevels = 7;
+
+// Probe-only multigrid arrays of one minibatch (Sec. 3.2, Eq. def_weights and
+// Eq. downsampled_terms).  Level l has side m >> l.
+//   G[l]  = conj(Q_l) / (u_l + |Q_l|^2)               (closed-form gain, 0/0 := 0)
+//   Q[l]  = I_h^H Q_{l-1} (Q[0] is the probe itself)
+//   Wz[l] = |Q_l|^2 / (I_H^h I_h^H |Q_l|^2)            (l < L-1)
+//   WR[l] = (I_H^h Q_{l+1}) conj(Q_l) / (I_H^h I_h^H |Q_l|^2)  (l < L-1)
+struct LevelArrays {
+  const float2* G[kMaxLevels];
+  const float2* Q[kMaxLevels];
+  const float* Wz[kMaxLevels];
+  const float2* WR[kMaxLevels];
+};
+
+struct PrepArgs {
+  const float2* probe;
+  int m, levels, prolong;
+  float alpha, w_eps;
+  float* wq;                    // [m*m] |Q|^2 + w_eps max|Q|^2 (object-combine weight)
+  float* u[kMaxLevels];         // per-level rPIE weight u_l (scratch)
+  float* T[kMaxLevels];         // per-level I_h^H |Q_l|^2 (side (m >> l) / 2, scratch)
+  float2* G[kMaxLevels];
+  float2* Q[kMaxLevels];        // Q[0] unused (the probe)
+  float* Wz[kMaxLevels];
+  float2* WR[kMaxLevels];
+};
+
+struct StepArgs {
+  const float2* object;
+  const float2* probe;
+  const int32_t* pos;
+  const float* amp;             // sqrt(max(d,0)) in the FFT's storage order, [N][m][m]
+  const int32_t* order;         // positions of this minibatch, [b]
+  int n_rows, n_cols;
+  int levels, prolong, joint, verify;
+  LevelArrays lv;
+  float2* zt;                   // [b][m*m] joint-step object patches z~_k
+  float2* qt;                   // [b][m*m] joint-step probes Q~_k
+  float* mu;                    // [b] max |z_k|^2
+  double* phi;                  // [b] Phi_k at the snapshot
+  double* phi_after;            // [b] Phi~_k(Q~, z~_k) (verify only)
+};
+
+struct ApplyArgs {
+  float2* object;
+  float2* probe;
+  const int32_t* pos;
+  const int32_t* order;
+  int b, n_rows, n_cols, m, combine;
+  const float2* zt;
+  const float2* qt;
+  const float* mu;
+  const float* wq;
+  int tiles_x, tiles_y;         // object tiles of 32 x 32 pixels
+};
+
+constexpr int kApplyTile = 32;
+constexpr int kApplyThreads = 256;
+
+cudaError_t upload_twiddles();
+cudaError_t launch_amp_prep(const float* d, float* amp, int m, int n_pos, cudaStream_t s);
+cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
+cudaError_t launch_step(int m, int b, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
+cudaError_t launch_misfit(int m, const float2* object, const float2* probe, const int32_t* pos,
+                          const float* amp, int n_rows, int n_cols, int n_pos, double* partial,
+                          cudaStream_t s);
+cudaError_t launch_sum(const double* x, int n, double scale, double* out, cudaStream_t s);
+cudaError_t launch_simulate(int m, const float2* object, const float2* probe, const int32_t* pos,
+                            int n_rows, int n_cols, int n_pos, float* out, cudaStream_t s);
+cudaError_t launch_fft2(int m, const float2* in, float2* out, int count, int inverse,
+                        cudaStream_t s);
+cudaError_t launch_normalize_probe(const float* amp, int m, int n_pos, float2* probe,
+                                   double* scratch, int scratch_len, cudaStream_t s);
+size_t step_smem_bytes(int m, int levels);
+int step_smem_limit();
+
+}  // namespace emg

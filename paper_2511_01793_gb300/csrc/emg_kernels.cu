@@ -1,0 +1,791 @@
+// Kernels of the eMAGPIE hot path (arXiv 2511.01793) for sm_103a.
+//
+//   k_amp_prep     a_k = sqrt(max(d_k, 0)) reordered into the FFT storage order
+//   k_prep         per-minibatch probe-only arrays: max|Q|^2, gains G_l, MAGPIE
+//                  weights W_z, W_R and restricted probes Q_l (Sec. 3.2)
+//   k_step<M>      one CTA per scan position: gather, exit wave, 2-D FFT, modulus
+//                  replacement (Def. 2.1), inverse FFT, MAGPIE object step,
+//                  ePIE probe step, geometric-mean joint step (Eq. geomean)
+//   k_apply        deterministic combine of the minibatch into object and probe
+//   k_misfit<M>    Phi_k = 1/2 ||Q . P_k z - R_k||^2 (Eq. exit_misfit), per position
+//   k_simulate<M>  d_k = |F(Q . P_k z)|^2 (Sec. 2.1 data model)
+//   k_fft2<M>      batched 2-D DFT of natural-order tiles
+#include <math.h>
+
+#include "emg_fft.cuh"
+#include "emg_internal.h"
+
+namespace emg {
+
+namespace {
+
+template <int M> struct StepThreads;
+template <> struct StepThreads<16> { static constexpr int value = 64; };
+template <> struct StepThreads<32> { static constexpr int value = 128; };
+template <> struct StepThreads<64> { static constexpr int value = 256; };
+template <> struct StepThreads<128> { static constexpr int value = 512; };
+
+__device__ __forceinline__ float2 czero() { return make_float2(0.f, 0.f); }
+
+__device__ __forceinline__ float2 gather_obj(const float2* __restrict__ z, int n_rows, int n_cols,
+                                             int gr, int gc) {
+  if ((unsigned)gr < (unsigned)n_rows && (unsigned)gc < (unsigned)n_cols)
+    return z[(size_t)gr * n_cols + gc];
+  return czero();
+}
+
+// num / den with 0/0 read as 0 (den == 0 gives 0).
+__device__ __forceinline__ float safe_div(float num, float den) { return den != 0.f ? num / den : 0.f; }
+__device__ __forceinline__ float2 safe_cdiv(float2 num, float den) {
+  return den != 0.f ? make_float2(num.x / den, num.y / den) : czero();
+}
+
+// Principal square root of w (Kahan, "Branch cuts for complex elementary functions", 1987).
+__device__ __forceinline__ float2 csqrt_principal(float2 w) {
+  const float mag = sqrtf(fmaf(w.x, w.x, w.y * w.y));
+  if (mag == 0.f) return czero();
+  const float t = sqrtf(0.5f * (fabsf(w.x) + mag));
+  if (w.x >= 0.f) return make_float2(t, w.y / (2.f * t));
+  return make_float2(fabsf(w.y) / (2.f * t), copysignf(t, w.y));
+}
+
+// y with y^2 = x * xp and Re(y conj(x)) >= 0 (Eq. geomean); ties keep the principal root.
+__device__ __forceinline__ float2 geometric_mean_aligned(float2 x, float2 xp) {
+  float2 y = csqrt_principal(cmul(x, xp));
+  if (fmaf(y.x, x.x, y.y * x.y) < 0.f) y = make_float2(-y.x, -y.y);
+  return y;
+}
+
+template <typename T>
+__device__ __forceinline__ T lerp4(T a, T b, T c, T d);
+template <>
+__device__ __forceinline__ float lerp4<float>(float a, float b, float c, float d) {
+  return 0.5625f * a + 0.1875f * b + 0.1875f * c + 0.0625f * d;
+}
+template <>
+__device__ __forceinline__ float2 lerp4<float2>(float2 a, float2 b, float2 c, float2 d) {
+  return make_float2(lerp4<float>(a.x, b.x, c.x, d.x), lerp4<float>(a.y, b.y, c.y, d.y));
+}
+
+// (I_H^h y)(r, c) for a coarse array of side mc with row stride `stride`.
+// kind 0: piecewise constant (4 (I_h^H)^T); kind 1: cell-centred bilinear, edge clamp.
+template <typename T>
+__device__ __forceinline__ T prolong_at(const T* y, int stride, int mc, int r, int c, int kind) {
+  const int i = r >> 1, j = c >> 1;
+  const T v = y[i * stride + j];
+  if (kind == 0) return v;
+  const int i2 = (r & 1) ? min(i + 1, mc - 1) : max(i - 1, 0);
+  const int j2 = (c & 1) ? min(j + 1, mc - 1) : max(j - 1, 0);
+  return lerp4<T>(v, y[i2 * stride + j], y[i * stride + j2], y[i2 * stride + j2]);
+}
+
+template <int NT>
+__device__ __forceinline__ float block_max(float v, float* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = sh[0];
+#pragma unroll
+  for (int i = 1; i < NT / 32; ++i) r = fmaxf(r, sh[i]);
+  __syncthreads();
+  return r;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = sh[0];
+#pragma unroll
+  for (int i = 1; i < NT / 32; ++i) r += sh[i];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// a_k in storage order: amp[k][e_r][e_c] = sqrt(max(d[k][f(e_r)][f(e_c)], 0)).
+template <int M>
+__global__ void k_amp_prep(const float* __restrict__ d, float* __restrict__ amp, int n_pos) {
+  const size_t total = (size_t)n_pos * M * M;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t k = i / (M * M);
+    const int e = (int)(i % (M * M));
+    const int er = e / M, ec = e % M;
+    const float v = d[k * M * M + storage_to_freq<M>(er) * M + storage_to_freq<M>(ec)];
+    amp[i] = sqrtf(fmaxf(v, 0.f));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Probe-only arrays of one minibatch (single CTA; O(m^2) work).
+constexpr int kPrepThreads = 1024;
+
+__global__ void __launch_bounds__(kPrepThreads) k_prep(const PrepArgs a) {
+  __shared__ float redf[kPrepThreads / 32];
+  const int tid = threadIdx.x;
+  const int m = a.m;
+  float mx = 0.f;
+  for (int p = tid; p < m * m; p += kPrepThreads) mx = fmaxf(mx, cabs2(a.probe[p]));
+  const float MQ = block_max<kPrepThreads>(mx, redf);
+
+  // level 0: u_0 = alpha (M_Q - |Q|^2), G_0, combine weight
+  for (int p = tid; p < m * m; p += kPrepThreads) {
+    const float2 q = a.probe[p];
+    const float a2 = cabs2(q);
+    const float u = a.alpha * (MQ - a2);
+    a.u[0][p] = u;
+    a.G[0][p] = safe_cdiv(cconj(q), u + a2);
+    a.wq[p] = fmaf(a.w_eps, MQ, a2);
+  }
+  for (int l = 0; l + 1 < a.levels; ++l) {
+    __syncthreads();
+    const int mf = m >> l, mc = mf >> 1;
+    const float2* Qf = (l == 0) ? a.probe : a.Q[l];
+    const float* uf = a.u[l];
+    // coarse: T = I_h^H |Q_l|^2, Q_{l+1} = I_h^H Q_l, u_{l+1} = W_u^H I_h^H u_l, G_{l+1}
+    for (int pc = tid; pc < mc * mc; pc += kPrepThreads) {
+      const int i = pc / mc, j = pc % mc;
+      float t = 0.f, ur = 0.f;
+      float2 qs = czero();
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+          const int pf = (2 * i + dy) * mf + 2 * j + dx;
+          const float2 q = Qf[pf];
+          t += cabs2(q);
+          qs = cadd(qs, q);
+          ur += uf[pf];
+        }
+      t *= 0.25f;
+      ur *= 0.25f;
+      qs = cscale(qs, 0.25f);
+      const float aH = cabs2(qs);
+      const float uH = safe_div(aH, t) * ur;
+      a.T[l][pc] = t;
+      a.Q[l + 1][pc] = qs;
+      a.u[l + 1][pc] = uH;
+      a.G[l + 1][pc] = safe_cdiv(cconj(qs), uH + aH);
+    }
+    __syncthreads();
+    // fine: W_z = |Q_l|^2 / S, W_R = (I_H^h Q_{l+1}) conj(Q_l) / S, S = I_H^h T
+    for (int pf = tid; pf < mf * mf; pf += kPrepThreads) {
+      const int r = pf / mf, c = pf % mf;
+      const float S = prolong_at<float>(a.T[l], mc, mc, r, c, a.prolong);
+      const float2 pq = prolong_at<float2>(a.Q[l + 1], mc, mc, r, c, a.prolong);
+      const float2 q = Qf[pf];
+      a.Wz[l][pf] = safe_div(cabs2(q), S);
+      a.WR[l][pf] = safe_cdiv(cmulc(pq, q), S);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One scan position per CTA.
+template <int M>
+__host__ __device__ constexpr size_t level_floats2(int l) {
+  return (size_t)(M >> l) * ((M >> l) + 1);
+}
+
+template <int M>
+__host__ __device__ inline size_t step_smem_elems(int levels) {
+  size_t n = level_floats2<M>(0);
+  for (int l = 1; l < levels; ++l) n += 2 * level_floats2<M>(l);
+  return n;
+}
+
+template <int M>
+__global__ void __launch_bounds__(StepThreads<M>::value) k_step(const StepArgs a) {
+  constexpr int NT = StepThreads<M>::value;
+  constexpr int S = M + 1;
+  constexpr int N1 = FftPlan<M>::N1, N2 = FftPlan<M>::N2;
+  extern __shared__ float2 sm[];
+  __shared__ double redd[NT / 32];
+  __shared__ float redf[NT / 32];
+  const int tid = threadIdx.x;
+  const int kb = blockIdx.x;
+  const int k = a.order[kb];
+  const int o_r = a.pos[2 * k], o_c = a.pos[2 * k + 1];
+  float2* buf = sm;
+
+  // a1: z_k = P_k z, psi = Q z_k, mu_k = max |z_k|^2
+  float mu_l = 0.f;
+  for (int p = tid; p < M * M; p += NT) {
+    const int r = p / M, c = p % M;
+    const float2 zk = gather_obj(a.object, a.n_rows, a.n_cols, o_r + r, o_c + c);
+    buf[r * S + c] = cmul(a.probe[p], zk);
+    mu_l = fmaxf(mu_l, cabs2(zk));
+  }
+  const float mu = block_max<NT>(mu_l, redf);
+
+  // a2: Psi = F psi (rows, then column pass A)
+  fft2_fwd_until_col_b<M, NT>(buf, tid);
+
+  // a2 (column pass B) + a3: Psi' = a_k Psi / |Psi| (scaled by 1/M^2) + a4 start
+  const float* amp = a.amp + (size_t)k * M * M;
+  const float inv_m2 = 1.f / (float)(M * M);
+  float acc = 0.f;
+  for (int s = tid; s < M * N2; s += NT) {
+    const int k2 = s / M, c = s % M;
+    float2 v[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) v[i] = buf[(i + N1 * k2) * S + c];
+    Dft<N1, false>::run(v);
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      const float am = amp[(i + N1 * k2) * M + c];
+      const float p2 = cabs2(v[i]);
+      if (p2 > 0.f) {
+        const float inv = rsqrtf(p2);
+        const float dm = fmaf(p2, inv, -am);
+        acc = fmaf(dm, dm, acc);
+        v[i] = cscale(v[i], am * inv * inv_m2);
+      } else {
+        acc = fmaf(am, am, acc);
+        v[i] = make_float2(am * inv_m2, 0.f);
+      }
+    }
+    Dft<N1, true>::run(v);
+#pragma unroll
+    for (int i = 0; i < N1; ++i) buf[(i + N1 * k2) * S + c] = v[i];
+  }
+  __syncthreads();
+  // a4: R = F^-1 Psi' (natural order)
+  fft2_inv_after_col_b<M, NT>(buf, tid);
+  const double phi = block_sum<NT>((double)acc, redd) * (0.5 / (double)(M * M));
+
+  // a5: MAGPIE multigrid object step, patch-local (levels > 1)
+  float2* Zl[kMaxLevels];
+  float2* Rl[kMaxLevels];
+  {
+    size_t off = level_floats2<M>(0);
+    for (int l = 1; l < a.levels; ++l) {
+      Zl[l] = sm + off;
+      off += level_floats2<M>(l);
+      Rl[l] = sm + off;
+      off += level_floats2<M>(l);
+    }
+  }
+  if (a.levels > 1) {
+    // restrict level 0 -> 1: z_1 = I_h^H (W_z z_k), R_1 = I_h^H (W_R R)
+    {
+      constexpr int mc = M / 2, sc = mc + 1;
+      const float* Wz = a.lv.Wz[0];
+      const float2* WR = a.lv.WR[0];
+      for (int p = tid; p < mc * mc; p += NT) {
+        const int i = p / mc, j = p % mc;
+        float2 zs = czero(), rs = czero();
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            const int r = 2 * i + dy, c = 2 * j + dx;
+            const float2 zk = gather_obj(a.object, a.n_rows, a.n_cols, o_r + r, o_c + c);
+            zs = cadd(zs, cscale(zk, Wz[r * M + c]));
+            rs = cadd(rs, cmul(WR[r * M + c], buf[r * S + c]));
+          }
+        Zl[1][i * sc + j] = cscale(zs, 0.25f);
+        Rl[1][i * sc + j] = cscale(rs, 0.25f);
+      }
+    }
+    __syncthreads();
+    for (int l = 1; l + 1 < a.levels; ++l) {
+      const int mf = M >> l, sf = mf + 1, mc = mf >> 1, sc = mc + 1;
+      const float* Wz = a.lv.Wz[l];
+      const float2* WR = a.lv.WR[l];
+      for (int p = tid; p < mc * mc; p += NT) {
+        const int i = p / mc, j = p % mc;
+        float2 zs = czero(), rs = czero();
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            const int r = 2 * i + dy, c = 2 * j + dx;
+            zs = cadd(zs, cscale(Zl[l][r * sf + c], Wz[r * mf + c]));
+            rs = cadd(rs, cmul(WR[r * mf + c], Rl[l][r * sf + c]));
+          }
+        Zl[l + 1][i * sc + j] = cscale(zs, 0.25f);
+        Rl[l + 1][i * sc + j] = cscale(rs, 0.25f);
+      }
+      __syncthreads();
+    }
+    // coarsest level: correction c = G (R - Q z), stored over z
+    {
+      const int l = a.levels - 1;
+      const int ml = M >> l, sl = ml + 1;
+      const float2* G = a.lv.G[l];
+      const float2* Q = a.lv.Q[l];
+      for (int p = tid; p < ml * ml; p += NT) {
+        const int i = p / ml, j = p % ml;
+        const float2 z = Zl[l][i * sl + j];
+        Zl[l][i * sl + j] = cmul(G[p], csub(Rl[l][i * sl + j], cmul(Q[p], z)));
+      }
+      __syncthreads();
+    }
+    // back up: c_l = I_H^h c_{l+1} + G_l (R_l - Q_l (z_l + I_H^h c_{l+1}))
+    for (int l = a.levels - 2; l >= 1; --l) {
+      const int ml = M >> l, sl = ml + 1, mc = ml >> 1, sc = mc + 1;
+      const float2* G = a.lv.G[l];
+      const float2* Q = a.lv.Q[l];
+      for (int p = tid; p < ml * ml; p += NT) {
+        const int i = p / ml, j = p % ml;
+        const float2 pro = prolong_at<float2>(Zl[l + 1], sc, mc, i, j, a.prolong);
+        const float2 zp = cadd(Zl[l][i * sl + j], pro);
+        Zl[l][i * sl + j] = cadd(pro, cmul(G[p], csub(Rl[l][i * sl + j], cmul(Q[p], zp))));
+      }
+      __syncthreads();
+    }
+  }
+
+  // a5 (finest level) + a6 + a7: z+, Q+, geometric-mean joint step
+  const float inv_mu = mu > 0.f ? 1.f / mu : 0.f;
+  const float2* G0 = a.lv.G[0];
+  float2* zt = a.zt + (size_t)kb * M * M;
+  float2* qt = a.qt + (size_t)kb * M * M;
+  float acc_after = 0.f;
+  for (int p = tid; p < M * M; p += NT) {
+    const int r = p / M, c = p % M;
+    const float2 zk = gather_obj(a.object, a.n_rows, a.n_cols, o_r + r, o_c + c);
+    const float2 q = a.probe[p];
+    const float2 R = buf[r * S + c];
+    const float2 res = csub(R, cmul(q, zk));
+    float2 zplus;
+    if (a.levels == 1) {
+      zplus = cadd(zk, cmul(G0[p], res));
+    } else {
+      constexpr int mc = M / 2, sc = mc + 1;
+      const float2 pro = prolong_at<float2>(Zl[1], sc, mc, r, c, a.prolong);
+      const float2 zp = cadd(zk, pro);
+      zplus = cadd(zp, cmul(G0[p], csub(R, cmul(q, zp))));
+    }
+    const float2 qplus = cadd(q, cscale(cconjmul(zk, res), inv_mu));
+    float2 zn, qn;
+    if (a.joint) {
+      zn = geometric_mean_aligned(zk, zplus);
+      qn = geometric_mean_aligned(q, qplus);
+    } else {
+      zn = zplus;
+      qn = qplus;
+    }
+    zt[p] = zn;
+    qt[p] = qn;
+    if (a.verify) acc_after += cabs2(csub(cmul(qn, zn), R));
+  }
+  double phi_after = 0.0;
+  if (a.verify) phi_after = 0.5 * block_sum<NT>((double)acc_after, redd);
+  if (tid == 0) {
+    a.mu[kb] = mu;
+    a.phi[kb] = phi;
+    if (a.verify) a.phi_after[kb] = phi_after;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a8 + a9: deterministic combine.  Blocks [0, tiles) own 32 x 32 object tiles;
+// the remaining blocks own 256 probe pixels each.
+__global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
+  extern __shared__ int list[];  // [b][3] = (kb, row, col) of patches overlapping the tile
+  __shared__ int warp_count[kApplyThreads / 32];
+  __shared__ int total;
+  const int tid = threadIdx.x;
+  const int n_tiles = a.tiles_x * a.tiles_y;
+  const int m = a.m;
+  if ((int)blockIdx.x < n_tiles) {
+    const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x % a.tiles_x;
+    const int r0 = ty * kApplyTile, c0 = tx * kApplyTile;
+    if (tid == 0) total = 0;
+    __syncthreads();
+    // ordered compaction of the minibatch patches that overlap this tile
+    for (int base = 0; base < a.b; base += kApplyThreads) {
+      const int kb = base + tid;
+      int pr = 0, pc = 0;
+      bool hit = false;
+      if (kb < a.b) {
+        const int k = a.order[kb];
+        pr = a.pos[2 * k];
+        pc = a.pos[2 * k + 1];
+        hit = pr < r0 + kApplyTile && pr + m > r0 && pc < c0 + kApplyTile && pc + m > c0;
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, hit);
+      const int lane = tid & 31, warp = tid >> 5;
+      if (lane == 0) warp_count[warp] = __popc(mask);
+      __syncthreads();
+      int off = total;
+      for (int w = 0; w < warp; ++w) off += warp_count[w];
+      if (hit) {
+        const int slot = off + __popc(mask & ((1u << lane) - 1u));
+        list[3 * slot] = kb;
+        list[3 * slot + 1] = pr;
+        list[3 * slot + 2] = pc;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        int t = total;
+        for (int w = 0; w < kApplyThreads / 32; ++w) t += warp_count[w];
+        total = t;
+      }
+      __syncthreads();
+    }
+    const int cnt = total;
+    if (cnt == 0) return;
+    for (int p = tid; p < kApplyTile * kApplyTile; p += kApplyThreads) {
+      const int row = r0 + p / kApplyTile, col = c0 + p % kApplyTile;
+      if (row >= a.n_rows || col >= a.n_cols) continue;
+      float2 num = czero();
+      float den = 0.f;
+      bool covered = false;
+      for (int t = 0; t < cnt; ++t) {
+        const int lr = row - list[3 * t + 1], lc = col - list[3 * t + 2];
+        if ((unsigned)lr < (unsigned)m && (unsigned)lc < (unsigned)m) {
+          const int kb = list[3 * t];
+          const float2 v = a.zt[(size_t)kb * m * m + lr * m + lc];
+          covered = true;
+          if (a.combine == 0) {
+            const float w = a.wq[lr * m + lc];
+            num = make_float2(fmaf(w, v.x, num.x), fmaf(w, v.y, num.y));
+            den += w;
+          } else {
+            num = cadd(num, v);
+            den += 1.f;
+          }
+        }
+      }
+      if (!covered) continue;
+      const size_t gi = (size_t)row * a.n_cols + col;
+      if (a.combine == 0) {
+        a.object[gi] = safe_cdiv(num, den);
+      } else {
+        const float2 z = a.object[gi];
+        a.object[gi] = cadd(z, csub(num, cscale(z, den)));
+      }
+    }
+  } else {
+    const int p = (blockIdx.x - n_tiles) * kApplyThreads + tid;
+    if (p >= m * m) return;
+    float2 s = czero();
+    int cnt = 0;
+    for (int kb = 0; kb < a.b; ++kb) {
+      if (a.mu[kb] > 0.f) {
+        s = cadd(s, a.qt[(size_t)kb * m * m + p]);
+        ++cnt;
+      }
+    }
+    if (cnt == 0) return;
+    if (a.combine == 0) {
+      a.probe[p] = cscale(s, 1.f / (float)cnt);
+    } else {
+      const float2 q = a.probe[p];
+      a.probe[p] = cadd(q, csub(s, cscale(q, (float)cnt)));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Phi_k = (1/2 M^2) sum (|F psi| - a_k)^2 per position (Parseval form of Eq. exit_misfit).
+template <int M>
+__global__ void __launch_bounds__(StepThreads<M>::value)
+    k_misfit(const float2* __restrict__ object, const float2* __restrict__ probe,
+             const int32_t* __restrict__ pos, const float* __restrict__ amp, int n_rows, int n_cols,
+             double* __restrict__ partial) {
+  constexpr int NT = StepThreads<M>::value;
+  constexpr int S = M + 1;
+  constexpr int N1 = FftPlan<M>::N1, N2 = FftPlan<M>::N2;
+  extern __shared__ float2 sm[];
+  __shared__ double redd[NT / 32];
+  const int tid = threadIdx.x;
+  const int k = blockIdx.x;
+  const int o_r = pos[2 * k], o_c = pos[2 * k + 1];
+  float2* buf = sm;
+  for (int p = tid; p < M * M; p += NT) {
+    const int r = p / M, c = p % M;
+    buf[r * S + c] = cmul(probe[p], gather_obj(object, n_rows, n_cols, o_r + r, o_c + c));
+  }
+  __syncthreads();
+  fft2_fwd_until_col_b<M, NT>(buf, tid);
+  const float* ak = amp + (size_t)k * M * M;
+  float acc = 0.f;
+  for (int s = tid; s < M * N2; s += NT) {
+    const int k2 = s / M, c = s % M;
+    float2 v[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) v[i] = buf[(i + N1 * k2) * S + c];
+    Dft<N1, false>::run(v);
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      const float dm = sqrtf(cabs2(v[i])) - ak[(i + N1 * k2) * M + c];
+      acc = fmaf(dm, dm, acc);
+    }
+  }
+  const double tot = block_sum<NT>((double)acc, redd);
+  if (tid == 0) partial[k] = tot * (0.5 / (double)(M * M));
+}
+
+// Deterministic single-block sum: out = scale * sum x[0..n).
+constexpr int kSumThreads = 1024;
+__global__ void __launch_bounds__(kSumThreads) k_sum(const double* __restrict__ x, int n,
+                                                     double scale, double* __restrict__ out) {
+  __shared__ double redd[kSumThreads / 32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += kSumThreads) s += x[i];
+  s = block_sum<kSumThreads>(s, redd);
+  if (threadIdx.x == 0) *out = s * scale;
+}
+
+// ---------------------------------------------------------------------------
+// Data model of Sec. 2.1: d_k = |F(Q . P_k z)|^2 in natural order.
+template <int M>
+__global__ void __launch_bounds__(StepThreads<M>::value)
+    k_simulate(const float2* __restrict__ object, const float2* __restrict__ probe,
+               const int32_t* __restrict__ pos, int n_rows, int n_cols, float* __restrict__ out) {
+  constexpr int NT = StepThreads<M>::value;
+  constexpr int S = M + 1;
+  extern __shared__ float2 sm[];
+  const int tid = threadIdx.x;
+  const int k = blockIdx.x;
+  const int o_r = pos[2 * k], o_c = pos[2 * k + 1];
+  float2* buf = sm;
+  for (int p = tid; p < M * M; p += NT) {
+    const int r = p / M, c = p % M;
+    buf[r * S + c] = cmul(probe[p], gather_obj(object, n_rows, n_cols, o_r + r, o_c + c));
+  }
+  __syncthreads();
+  fft2_fwd_until_col_b<M, NT>(buf, tid);
+  pass_b<M, true, NT, false>(buf, tid);
+  __syncthreads();
+  float* dk = out + (size_t)k * M * M;
+  for (int p = tid; p < M * M; p += NT) {
+    const int er = p / M, ec = p % M;
+    dk[storage_to_freq<M>(er) * M + storage_to_freq<M>(ec)] = cabs2(buf[er * S + ec]);
+  }
+}
+
+// Batched 2-D DFT of natural-order tiles.
+template <int M>
+__global__ void __launch_bounds__(StepThreads<M>::value)
+    k_fft2(const float2* in, float2* out, int inverse) {
+  constexpr int NT = StepThreads<M>::value;
+  constexpr int S = M + 1;
+  extern __shared__ float2 sm[];
+  const int tid = threadIdx.x;
+  const float2* x = in + (size_t)blockIdx.x * M * M;
+  float2* y = out + (size_t)blockIdx.x * M * M;
+  float2* buf = sm;
+  if (!inverse) {
+    for (int p = tid; p < M * M; p += NT) buf[(p / M) * S + p % M] = x[p];
+    __syncthreads();
+    fft2_fwd_until_col_b<M, NT>(buf, tid);
+    pass_b<M, true, NT, false>(buf, tid);
+    __syncthreads();
+    for (int p = tid; p < M * M; p += NT) {
+      const int er = p / M, ec = p % M;
+      y[storage_to_freq<M>(er) * M + storage_to_freq<M>(ec)] = buf[er * S + ec];
+    }
+  } else {
+    const float s = 1.f / (float)(M * M);
+    for (int p = tid; p < M * M; p += NT) {
+      const int er = p / M, ec = p % M;
+      buf[er * S + ec] = cscale(x[storage_to_freq<M>(er) * M + storage_to_freq<M>(ec)], s);
+    }
+    __syncthreads();
+    pass_b<M, true, NT, true>(buf, tid);
+    __syncthreads();
+    fft2_inv_after_col_b<M, NT>(buf, tid);
+    for (int p = tid; p < M * M; p += NT) y[p] = buf[(p / M) * S + p % M];
+  }
+}
+
+// dp_avg probe scaling (Sec. 4.1): partial sums of a^2 = max(d, 0).
+constexpr int kNormThreads = 256;
+__global__ void __launch_bounds__(kNormThreads) k_sum_sq(const float* __restrict__ amp, size_t n,
+                                                         double* __restrict__ partial) {
+  __shared__ double redd[kNormThreads / 32];
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)kNormThreads + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * kNormThreads) {
+    const float v = amp[i];
+    s += (double)(v * v);
+  }
+  s = block_sum<kNormThreads>(s, redd);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kSumThreads) k_scale_probe(const double* __restrict__ partial,
+                                                             int n_partial, int m, int n_pos,
+                                                             float2* __restrict__ probe) {
+  __shared__ double redd[kSumThreads / 32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n_partial; i += kSumThreads) s += partial[i];
+  const double sum_d = block_sum<kSumThreads>(s, redd);
+  double q2 = 0.0;
+  for (int p = threadIdx.x; p < m * m; p += kSumThreads) q2 += (double)cabs2(probe[p]);
+  const double norm2 = block_sum<kSumThreads>(q2, redd);
+  const double dp_avg = sqrt(sum_d / (double)n_pos) / (double)m;
+  const float scale = norm2 > 0.0 ? (float)(dp_avg / sqrt(norm2)) : 0.f;
+  for (int p = threadIdx.x; p < m * m; p += kSumThreads) probe[p] = cscale(probe[p], scale);
+}
+
+template <int M>
+cudaError_t set_step_smem() {
+  return cudaFuncSetAttribute(k_step<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              step_smem_limit());
+}
+
+template <int M>
+cudaError_t launch_step_t(int b, const StepArgs& a, cudaStream_t s) {
+  const size_t bytes = step_smem_elems<M>(a.levels) * sizeof(float2);
+  k_step<M><<<b, StepThreads<M>::value, bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_misfit_t(const float2* object, const float2* probe, const int32_t* pos,
+                            const float* amp, int n_rows, int n_cols, int n_pos, double* partial,
+                            cudaStream_t s) {
+  const size_t bytes = level_floats2<M>(0) * sizeof(float2);
+  k_misfit<M><<<n_pos, StepThreads<M>::value, bytes, s>>>(object, probe, pos, amp, n_rows, n_cols,
+                                                          partial);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_simulate_t(const float2* object, const float2* probe, const int32_t* pos,
+                              int n_rows, int n_cols, int n_pos, float* out, cudaStream_t s) {
+  const size_t bytes = level_floats2<M>(0) * sizeof(float2);
+  k_simulate<M><<<n_pos, StepThreads<M>::value, bytes, s>>>(object, probe, pos, n_rows, n_cols, out);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_fft2_t(const float2* in, float2* out, int count, int inverse, cudaStream_t s) {
+  const size_t bytes = level_floats2<M>(0) * sizeof(float2);
+  k_fft2<M><<<count, StepThreads<M>::value, bytes, s>>>(in, out, inverse);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t set_aux_smem() {
+  const int bytes = (int)(level_floats2<M>(0) * sizeof(float2));
+  cudaError_t e = cudaFuncSetAttribute(k_misfit<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_simulate<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fft2<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
+#define EMG_DISPATCH_M(m, CALL)        \
+  switch (m) {                         \
+    case 16: { constexpr int M = 16; return CALL; }   \
+    case 32: { constexpr int M = 32; return CALL; }   \
+    case 64: { constexpr int M = 64; return CALL; }   \
+    case 128: { constexpr int M = 128; return CALL; } \
+    default: return cudaErrorInvalidValue;            \
+  }
+
+}  // namespace
+
+// Dynamic shared memory per CTA; 227 KB minus room for the kernels' static reductions.
+int step_smem_limit() { return 227 * 1024 - 1024; }
+
+size_t step_smem_bytes(int m, int levels) {
+  switch (m) {
+    case 16: return step_smem_elems<16>(levels) * sizeof(float2);
+    case 32: return step_smem_elems<32>(levels) * sizeof(float2);
+    case 64: return step_smem_elems<64>(levels) * sizeof(float2);
+    case 128: return step_smem_elems<128>(levels) * sizeof(float2);
+    default: return 0;
+  }
+}
+
+cudaError_t upload_twiddles() {
+  float2 h[256];
+  for (int t = 0; t < 256; ++t) {
+    const double ang = -2.0 * M_PI * (double)t / 256.0;
+    double c = cos(ang), s = sin(ang);
+    if (fabs(c) < 1e-15) c = 0.0;
+    if (fabs(s) < 1e-15) s = 0.0;
+    h[t] = make_float2((float)c, (float)s);
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_twiddle, h, sizeof(h));
+  if (e != cudaSuccess) return e;
+  if ((e = set_step_smem<16>()) != cudaSuccess) return e;
+  if ((e = set_step_smem<32>()) != cudaSuccess) return e;
+  if ((e = set_step_smem<64>()) != cudaSuccess) return e;
+  if ((e = set_step_smem<128>()) != cudaSuccess) return e;
+  if ((e = set_aux_smem<16>()) != cudaSuccess) return e;
+  if ((e = set_aux_smem<32>()) != cudaSuccess) return e;
+  if ((e = set_aux_smem<64>()) != cudaSuccess) return e;
+  if ((e = set_aux_smem<128>()) != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  return e;
+}
+
+cudaError_t launch_amp_prep(const float* d, float* amp, int m, int n_pos, cudaStream_t s) {
+  const size_t total = (size_t)n_pos * m * m;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  switch (m) {
+    case 16: k_amp_prep<16><<<blocks, 256, 0, s>>>(d, amp, n_pos); break;
+    case 32: k_amp_prep<32><<<blocks, 256, 0, s>>>(d, amp, n_pos); break;
+    case 64: k_amp_prep<64><<<blocks, 256, 0, s>>>(d, amp, n_pos); break;
+    case 128: k_amp_prep<128><<<blocks, 256, 0, s>>>(d, amp, n_pos); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
+  k_prep<<<1, kPrepThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step(int m, int b, const StepArgs& a, cudaStream_t s) {
+  EMG_DISPATCH_M(m, (launch_step_t<M>(b, a, s)));
+}
+
+cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
+  const int n_tiles = a.tiles_x * a.tiles_y;
+  const int n_probe = (a.m * a.m + kApplyThreads - 1) / kApplyThreads;
+  const size_t bytes = (size_t)a.b * 3 * sizeof(int);
+  k_apply<<<n_tiles + n_probe, kApplyThreads, bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_misfit(int m, const float2* object, const float2* probe, const int32_t* pos,
+                          const float* amp, int n_rows, int n_cols, int n_pos, double* partial,
+                          cudaStream_t s) {
+  EMG_DISPATCH_M(m, (launch_misfit_t<M>(object, probe, pos, amp, n_rows, n_cols, n_pos, partial, s)));
+}
+
+cudaError_t launch_sum(const double* x, int n, double scale, double* out, cudaStream_t s) {
+  k_sum<<<1, kSumThreads, 0, s>>>(x, n, scale, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_simulate(int m, const float2* object, const float2* probe, const int32_t* pos,
+                            int n_rows, int n_cols, int n_pos, float* out, cudaStream_t s) {
+  EMG_DISPATCH_M(m, (launch_simulate_t<M>(object, probe, pos, n_rows, n_cols, n_pos, out, s)));
+}
+
+cudaError_t launch_fft2(int m, const float2* in, float2* out, int count, int inverse,
+                        cudaStream_t s) {
+  EMG_DISPATCH_M(m, (launch_fft2_t<M>(in, out, count, inverse, s)));
+}
+
+cudaError_t launch_normalize_probe(const float* amp, int m, int n_pos, float2* probe,
+                                   double* scratch, int scratch_len, cudaStream_t s) {
+  const size_t n = (size_t)n_pos * m * m;
+  int blocks = (int)((n + kNormThreads - 1) / kNormThreads);
+  if (blocks > scratch_len) blocks = scratch_len;
+  k_sum_sq<<<blocks, kNormThreads, 0, s>>>(amp, n, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_scale_probe<<<1, kSumThreads, 0, s>>>(scratch, blocks, m, n_pos, probe);
+  return cudaGetLastError();
+}
+
+}  // namespace emg
