@@ -38,7 +38,7 @@ WORKLOAD = "mg_n512_m128"
 METRIC = "scan positions/sec per eMAGPIE epoch"
 UNIT = "positions/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_mg_n512_m128.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2511_01793_gb300", "csrc", f)
                   for f in ("emg_kernels.cu", "emg_fft.cuh", "emg_internal.h")]
 
@@ -87,12 +87,20 @@ def measured_peaks():
 
 
 def recorded_traffic():
-    """DRAM bytes per step-kernel launch from the last ncu capture, if still current."""
+    """DRAM bytes per step-kernel launch from the committed ncu summary, if still current.
+
+    The summary carries "kernel_hash: <h>" and "dram_bytes_per_launch: <n>" lines;
+    the figure is dropped (None) once the kernel sources have changed since.
+    """
     try:
+        fields = {}
         with open(TRAFFIC_FILE) as f:
-            t = json.load(f)
-        if t.get("kernel_hash") == kernel_hash():
-            return float(t["dram_bytes_per_launch"])
+            for line in f:
+                if ":" in line and not line.startswith(("|", "#", " ")):
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip()
+        if fields.get("kernel_hash") == kernel_hash():
+            return float(fields["dram_bytes_per_launch"])
     except Exception:
         pass
     return None
