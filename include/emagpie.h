@@ -232,6 +232,41 @@ emg_status emg_fft2(const float* in, float* out, int32_t m, int32_t count, int32
 emg_status emg_set_profiling(emg_ctx* ctx, int32_t enable);
 emg_status emg_profile_read(emg_ctx* ctx, double* ms, int64_t* launches);
 
+/*
+ * Allocation-free variant of emg_step_minibatch, without a context.  The paper
+ * has no counterpart: it exists for callers that may not allocate device
+ * memory (code running inside a memory pool or arena it does not own, code
+ * whose device footprint must not grow after start-up, or code under a policy
+ * that forbids cudaMalloc on its hot path).  The caller passes every input and
+ * output; the call performs no device or pinned allocation of any kind.
+ *
+ *  object      device complex64 [n_rows][n_cols], updated in place
+ *  probe       device complex64 [m][m], updated in place
+ *  pos         device int32 [n_pos][2] patch corners, |row|, |col| < 2^24
+ *  intensity   device float32 [n_pos][m][m] data d_k in natural order (DC at [0][0])
+ *  idx, b      host int32 [b] positions of this minibatch, 1 <= b <= n_pos
+ *  params      as for emg_create (minibatch and seed are ignored)
+ *
+ * The result equals emg_step_minibatch on the same inputs.  Its only scratch
+ * is one fixed device array of EMG_NOALLOC_SCRATCH_BYTES per GPU, part of the
+ * library image, held until the process exits.  A call needs about
+ * m^2 (16 b + 45) bytes of it; a larger request is rejected with EMG_EINVAL
+ * before any work is enqueued (at m = 128 that allows b <= 29, at m = 32
+ * b <= 500).  No part of the scratch needs to start at zero: each call writes
+ * every element it later reads.  All calls share the array, so calls that
+ * overlap on the GPU (other streams or threads) race and give wrong results;
+ * serialise them.  The first call on each device does a one-time set-up with
+ * that device current (constant tables, kernel attributes, the scratch
+ * address); make that first call before any stream capture.  Asynchronous on
+ * `stream` otherwise (the host idx array is copied before the call returns).
+ */
+#define EMG_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+emg_status emg_step_minibatch_noalloc(float* object, int32_t n_rows, int32_t n_cols,
+                                      float* probe, int32_t m, const int32_t* pos,
+                                      const float* intensity, int32_t n_pos,
+                                      const int32_t* idx, int32_t b,
+                                      const emg_params* params, emg_stream_t stream);
+
 /* Message of the last failure on this context (static until the next call). */
 emg_status emg_last_error(const emg_ctx* ctx, const char** msg);
 

@@ -26,7 +26,8 @@ __all__ = [
     "emg_create", "emg_set_intensity", "emg_bind_state", "emg_normalize_probe",
     "emg_step_minibatch", "emg_position_stats", "emg_set_verify", "emg_run_epochs", "emg_misfit",
     "emg_set_epoch", "emg_schedule_permutation", "emg_reconstruct_host",
-    "emg_simulate_intensity", "emg_fft2", "emg_set_profiling", "emg_profile_read",
+    "emg_simulate_intensity", "emg_fft2", "emg_step_minibatch_noalloc", "emg_set_profiling",
+    "emg_profile_read",
     "emg_last_error", "emg_destroy", "Context",
 ]
 
@@ -80,6 +81,9 @@ _SIGS = {
     "emg_simulate_intensity": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_int32,
                                               _VP, ctypes.c_int32, _VP, _VP]),
     "emg_fft2": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP]),
+    "emg_step_minibatch_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_int32,
+                                                  _VP, _VP, ctypes.c_int32, _I32P, ctypes.c_int32,
+                                                  ctypes.POINTER(EmgParams), _VP]),
     "emg_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "emg_profile_read": (ctypes.c_int, [_VP, _F64P, ctypes.POINTER(ctypes.c_int64)]),
     "emg_last_error": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_char_p)]),
@@ -250,6 +254,17 @@ def emg_simulate_intensity(object_ptr: int, n_rows: int, n_cols: int, probe_ptr:
 
 def emg_fft2(in_ptr: int, out_ptr: int, m: int, count: int, inverse: bool, stream: int = 0) -> None:
     _check(load().emg_fft2(in_ptr, out_ptr, m, count, int(bool(inverse)), _VP(stream)), "emg_fft2")
+
+
+def emg_step_minibatch_noalloc(object_ptr: int, n_rows: int, n_cols: int, probe_ptr: int, m: int,
+                               pos_ptr: int, intensity_ptr: int, n_pos: int, idx,
+                               params: EmgParams, stream: int = 0) -> None:
+    """Allocation-free minibatch step (no context); see include/emagpie.h."""
+    a = _i32(idx)
+    _check(load().emg_step_minibatch_noalloc(object_ptr, n_rows, n_cols, probe_ptr, m, pos_ptr,
+                                             intensity_ptr, n_pos, _ptr_i32(a), len(a),
+                                             ctypes.byref(params), _VP(stream)),
+           "emg_step_minibatch_noalloc")
 
 
 def emg_set_profiling(ctx: int, enable: bool) -> None:

@@ -198,7 +198,10 @@ __host__ __device__ inline size_t step_smem_elems(int levels) {
   return n;
 }
 
-template <int M>
+// NATURAL_AMP = true is the variant used by the allocation-free entry point:
+// a.amp then holds the caller's intensities d_k in natural order and the
+// amplitude sqrt(max(d, 0)) is formed on the fly.
+template <int M, bool NATURAL_AMP = false>
 __global__ void __launch_bounds__(StepThreads<M>::value) k_step(const StepArgs a) {
   constexpr int NT = StepThreads<M>::value;
   constexpr int S = M + 1;
@@ -237,7 +240,9 @@ __global__ void __launch_bounds__(StepThreads<M>::value) k_step(const StepArgs a
     Dft<N1, false>::run(v);
 #pragma unroll
     for (int i = 0; i < N1; ++i) {
-      const float am = amp[(i + N1 * k2) * M + c];
+      const float am = NATURAL_AMP
+                           ? sqrtf(fmaxf(amp[storage_to_freq<M>(i + N1 * k2) * M + storage_to_freq<M>(c)], 0.f))
+                           : amp[(i + N1 * k2) * M + c];
       const float p2 = cabs2(v[i]);
       if (p2 > 0.f) {
         const float inv = rsqrtf(p2);
@@ -789,3 +794,196 @@ cudaError_t launch_normalize_probe(const float* amp, int m, int n_pos, float2* p
 }
 
 }  // namespace emg
+
+// ===========================================================================
+// Allocation-free minibatch step: emg_step_minibatch_noalloc (include/emagpie.h).
+//
+// For callers that may not allocate device memory: code that runs inside a
+// memory pool or arena it does not own, code that must not grow the device
+// footprint after start-up, or code under a host-side policy that forbids
+// cudaMalloc on its hot path.  They pass every input and output; the only
+// scratch is the fixed array below, which every GPU that loads this library
+// holds until the process exits.
+// ===========================================================================
+#include <mutex>
+
+#include "../../include/emagpie.h"
+
+namespace emg {
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[EMG_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_base[256] = {nullptr};
+
+struct NoAllocLayout {
+  size_t idx, wq, zt, qt, mu, phi, phi_after, total;
+  size_t G[kMaxLevels], Q[kMaxLevels], u[kMaxLevels], Wz[kMaxLevels], WR[kMaxLevels], T[kMaxLevels];
+};
+
+// Byte offsets of every scratch array of one call, each 256-byte aligned.
+NoAllocLayout noalloc_layout(int m, int levels, int b) {
+  NoAllocLayout L{};
+  size_t bytes = 0;
+  auto take = [&](size_t n) {
+    const size_t off = (bytes + 255) & ~(size_t)255;
+    bytes = off + n;
+    return off;
+  };
+  L.idx = take((size_t)b * sizeof(int32_t));
+  for (int l = 0; l < levels; ++l) {
+    const size_t n = (size_t)(m >> l) * (m >> l);
+    L.G[l] = take(n * sizeof(float2));
+    L.Q[l] = take(n * sizeof(float2));
+    L.u[l] = take(n * sizeof(float));
+    if (l + 1 < levels) {
+      L.Wz[l] = take(n * sizeof(float));
+      L.WR[l] = take(n * sizeof(float2));
+      L.T[l] = take(n / 4 * sizeof(float));
+    }
+  }
+  L.wq = take((size_t)m * m * sizeof(float));
+  L.zt = take((size_t)b * m * m * sizeof(float2));
+  L.qt = take((size_t)b * m * m * sizeof(float2));
+  L.mu = take((size_t)b * sizeof(float));
+  L.phi = take((size_t)b * sizeof(double));
+  L.phi_after = take((size_t)b * sizeof(double));
+  L.total = bytes;
+  return L;
+}
+
+// Once per device, with that device current: twiddles, kernel attributes and
+// the device address of the scratch array (a host-side name of a __device__
+// array is not a device address, so it is looked up here).
+cudaError_t noalloc_setup(int dev, unsigned char** base) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  if (g_noalloc_base[dev]) {
+    *base = g_noalloc_base[dev];
+    return cudaSuccess;
+  }
+  cudaError_t e = upload_twiddles();
+  if (e != cudaSuccess) return e;
+  const int lim = step_smem_limit();
+  if ((e = cudaFuncSetAttribute(k_step<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) ||
+      (e = cudaFuncSetAttribute(k_step<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) ||
+      (e = cudaFuncSetAttribute(k_step<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) ||
+      (e = cudaFuncSetAttribute(k_step<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)))
+    return e;
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  g_noalloc_base[dev] = (unsigned char*)p;
+  *base = (unsigned char*)p;
+  return cudaSuccess;
+}
+
+template <int M>
+cudaError_t launch_step_natural(int b, const StepArgs& a, cudaStream_t s) {
+  const size_t bytes = step_smem_elems<M>(a.levels) * sizeof(float2);
+  k_step<M, true><<<b, StepThreads<M>::value, bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace emg
+
+extern "C" emg_status emg_step_minibatch_noalloc(float* object, int32_t n_rows, int32_t n_cols,
+                                                 float* probe, int32_t m, const int32_t* pos,
+                                                 const float* intensity, int32_t n_pos,
+                                                 const int32_t* idx, int32_t b,
+                                                 const emg_params* p, emg_stream_t stream) {
+  using namespace emg;
+  if (!object || !probe || !pos || !intensity || !idx || !p) return EMG_EINVAL;
+  if (n_rows < 1 || n_cols < 1 || n_pos < 1 || b < 1 || b > n_pos) return EMG_EINVAL;
+  if (m != 16 && m != 32 && m != 64 && m != 128) return EMG_ENOTSUP;
+  if (!(p->alpha > 0.f) || !isfinite(p->alpha) || !(p->w_eps >= 0.f) || !isfinite(p->w_eps))
+    return EMG_EINVAL;
+  if (p->levels < 1 || p->levels > kMaxLevels || (m >> (p->levels - 1)) < 2) return EMG_EINVAL;
+  if (p->prolong != EMG_PROLONG_CONST && p->prolong != EMG_PROLONG_BILINEAR) return EMG_EINVAL;
+  if (p->combine != EMG_COMBINE_WAVG && p->combine != EMG_COMBINE_SUM) return EMG_EINVAL;
+  if (p->joint != 0 && p->joint != 1) return EMG_EINVAL;
+  if (p->scatter != EMG_SCATTER_DETERMINISTIC) return EMG_ENOTSUP;
+  if (step_smem_bytes(m, p->levels) > (size_t)step_smem_limit()) return EMG_ENOTSUP;
+  for (int i = 0; i < b; ++i)
+    if (idx[i] < 0 || idx[i] >= n_pos) return EMG_EINVAL;
+  const NoAllocLayout L = noalloc_layout(m, p->levels, b);
+  if (L.total > (size_t)EMG_NOALLOC_SCRATCH_BYTES) return EMG_EINVAL;  // beyond the fixed scratch
+
+  int dev = 0;
+  unsigned char* base = nullptr;
+  if (cudaGetDevice(&dev) != cudaSuccess || noalloc_setup(dev, &base) != cudaSuccess) return EMG_ECUDA;
+  const cudaStream_t s = (cudaStream_t)stream;
+  int32_t* d_idx = (int32_t*)(base + L.idx);
+  if (cudaMemcpyAsync(d_idx, idx, (size_t)b * sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return EMG_ECUDA;
+
+  PrepArgs pa{};
+  StepArgs sa{};
+  pa.probe = (const float2*)probe;
+  pa.m = m;
+  pa.levels = p->levels;
+  pa.prolong = p->prolong;
+  pa.alpha = p->alpha;
+  pa.w_eps = p->w_eps;
+  pa.wq = (float*)(base + L.wq);
+  for (int l = 0; l < p->levels; ++l) {
+    pa.G[l] = (float2*)(base + L.G[l]);
+    pa.Q[l] = (float2*)(base + L.Q[l]);
+    pa.u[l] = (float*)(base + L.u[l]);
+    sa.lv.G[l] = pa.G[l];
+    sa.lv.Q[l] = pa.Q[l];
+    if (l + 1 < p->levels) {
+      pa.Wz[l] = (float*)(base + L.Wz[l]);
+      pa.WR[l] = (float2*)(base + L.WR[l]);
+      pa.T[l] = (float*)(base + L.T[l]);
+      sa.lv.Wz[l] = pa.Wz[l];
+      sa.lv.WR[l] = pa.WR[l];
+    }
+  }
+  sa.object = (const float2*)object;
+  sa.probe = (const float2*)probe;
+  sa.pos = pos;
+  sa.amp = intensity;
+  sa.order = d_idx;
+  sa.n_rows = n_rows;
+  sa.n_cols = n_cols;
+  sa.levels = p->levels;
+  sa.prolong = p->prolong;
+  sa.joint = p->joint;
+  sa.verify = 0;
+  sa.zt = (float2*)(base + L.zt);
+  sa.qt = (float2*)(base + L.qt);
+  sa.mu = (float*)(base + L.mu);
+  sa.phi = (double*)(base + L.phi);
+  sa.phi_after = (double*)(base + L.phi_after);
+  ApplyArgs aa{};
+  aa.object = (float2*)object;
+  aa.probe = (float2*)probe;
+  aa.pos = pos;
+  aa.order = d_idx;
+  aa.b = b;
+  aa.n_rows = n_rows;
+  aa.n_cols = n_cols;
+  aa.m = m;
+  aa.combine = p->combine;
+  aa.zt = sa.zt;
+  aa.qt = sa.qt;
+  aa.mu = sa.mu;
+  aa.wq = pa.wq;
+  aa.tiles_x = (n_cols + kApplyTile - 1) / kApplyTile;
+  aa.tiles_y = (n_rows + kApplyTile - 1) / kApplyTile;
+
+  cudaError_t e = launch_prep(pa, s);
+  if (e == cudaSuccess) {
+    switch (m) {
+      case 16: e = launch_step_natural<16>(b, sa, s); break;
+      case 32: e = launch_step_natural<32>(b, sa, s); break;
+      case 64: e = launch_step_natural<64>(b, sa, s); break;
+      default: e = launch_step_natural<128>(b, sa, s); break;
+    }
+  }
+  if (e == cudaSuccess) e = launch_apply(aa, s);
+  return e == cudaSuccess ? EMG_OK : EMG_ECUDA;
+}
