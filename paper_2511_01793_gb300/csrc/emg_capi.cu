@@ -45,6 +45,7 @@ struct emg_ctx {
   double* d_partial = nullptr;    // [N] misfit partials
   double* d_scalar = nullptr;     // [64] assorted scalar results
   double* d_norm = nullptr;       // [1024] normalisation partials
+  unsigned* d_mq = nullptr;       // [2] max|Q|^2 slots (float bits), alternating per minibatch
   float* d_wq = nullptr;          // [m][m]
   void* d_levels = nullptr;       // all multigrid arrays
   int32_t* d_orders = nullptr;    // [cap_orders]
@@ -175,6 +176,7 @@ void free_all(emg_ctx* c) {
   cudaFree(c->d_partial);
   cudaFree(c->d_scalar);
   cudaFree(c->d_norm);
+  cudaFree(c->d_mq);
   cudaFree(c->d_wq);
   cudaFree(c->d_levels);
   cudaFree(c->d_orders);
@@ -279,11 +281,24 @@ void permutation(uint64_t seed, int64_t epoch, int32_t n, int32_t* out) {
   }
 }
 
-// Enqueues one minibatch: probe prep, per-position step, combine.
-emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_phi_out) {
+// Seeds max|Q|^2 of the bound probe into slot 0 before a call's first minibatch.
+emg_status seed_probe_max(emg_ctx* c) {
+  EMG_CUDA(c, cudaMemsetAsync(c->d_mq, 0, 2 * sizeof(unsigned), c->stream));
+  LaunchMark mk(c, kKindOther);
+  cudaError_t e = emg::launch_probe_max(c->probe, c->m, c->d_mq, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_probe_max launch");
+  return EMG_OK;
+}
+
+// Enqueues one minibatch: probe prep, per-position step, combine.  `seq` is the
+// minibatch's index within the current call: it selects which max|Q|^2 slot
+// the prep reads and which one the combine fills.
+emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_phi_out, int seq) {
   if (!c->object || !c->probe) return fail(c, EMG_EINVAL, "no state bound");
   PrepArgs pa = c->prep;
   pa.probe = c->probe;  // the probe bound right now (emg_reconstruct_host swaps it)
+  pa.mq_read = c->d_mq + (seq & 1);
+  pa.mq_next = c->d_mq + ((seq + 1) & 1);
   cudaError_t e;
   {
     LaunchMark mk(c, kKindPrep);
@@ -327,6 +342,7 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   aa.qt = c->d_qt;
   aa.mu = c->d_mu;
   aa.wq = c->d_wq;
+  aa.mq_next = c->d_mq + ((seq + 1) & 1);
   aa.tiles_x = (c->n_cols + emg::kApplyTile - 1) / emg::kApplyTile;
   aa.tiles_y = (c->n_rows + emg::kApplyTile - 1) / emg::kApplyTile;
   {
@@ -366,11 +382,13 @@ emg_status run_epochs_impl(emg_ctx* c, int32_t n_epochs, const int32_t* order, d
   if (st != EMG_OK) return st;
   if ((st = ensure_hist(c, n_epochs)) != EMG_OK) return st;
   EMG_CUDA(c, cudaMemcpyAsync(c->d_orders, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  if ((st = seed_probe_max(c)) != EMG_OK) return st;
+  int seq = 0;
   for (int32_t e = 0; e < n_epochs; ++e) {
     const int32_t* ord = c->d_orders + (size_t)e * N;
     for (int b0 = 0; b0 < N; b0 += B) {
       const int b = (N - b0 < B) ? N - b0 : B;
-      if ((st = enqueue_minibatch(c, ord + b0, b, c->d_phi + b0)) != EMG_OK) return st;
+      if ((st = enqueue_minibatch(c, ord + b0, b, c->d_phi + b0, seq++)) != EMG_OK) return st;
     }
     if (running) {
       c->launches[kKindOther] += 1;
@@ -483,7 +501,7 @@ emg_status emg_create(emg_ctx** out, const emg_problem* pr, const emg_params* pa
       dmalloc(&c->d_zt, (size_t)B * mm) || dmalloc(&c->d_qt, (size_t)B * mm) ||
       dmalloc(&c->d_mu, (size_t)B) || dmalloc(&c->d_phi, (size_t)N) ||
       dmalloc(&c->d_phi_after, (size_t)B) || dmalloc(&c->d_partial, (size_t)N) ||
-      dmalloc(&c->d_scalar, (size_t)64) || dmalloc(&c->d_norm, (size_t)1024) ||
+      dmalloc(&c->d_scalar, (size_t)64) || dmalloc(&c->d_norm, (size_t)1024) || dmalloc(&c->d_mq, (size_t)2) ||
       dmalloc(&c->d_wq, mm))
     return bail(EMG_ENOMEM);
   if (cudaMallocHost(&c->h_scalar, 64 * sizeof(double)) != cudaSuccess) return bail(EMG_ENOMEM);
@@ -542,7 +560,8 @@ emg_status emg_step_minibatch(emg_ctx* c, const int32_t* idx, int32_t b, double*
   DeviceGuard g(c->device);
   if ((st = ensure_orders(c, (size_t)c->n_pos)) != EMG_OK) return st;
   EMG_CUDA(c, cudaMemcpyAsync(c->d_orders, idx, (size_t)b * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
-  if ((st = enqueue_minibatch(c, c->d_orders, b, c->d_phi)) != EMG_OK) return st;
+  if ((st = seed_probe_max(c)) != EMG_OK) return st;
+  if ((st = enqueue_minibatch(c, c->d_orders, b, c->d_phi, 0)) != EMG_OK) return st;
   c->last_b = b;
   if (sampled_misfit) {
     cudaError_t e = emg::launch_sum(c->d_phi, b, 1.0, c->d_scalar, c->stream);

@@ -97,63 +97,79 @@ __host__ __device__ __forceinline__ int storage_to_freq(int e) {
   return e / FftPlan<M>::N1 + FftPlan<M>::N2 * (e % FftPlan<M>::N1);
 }
 
-template <int M, bool COL>
-__device__ __forceinline__ int tile_addr(int line, int e) {
-  return COL ? e * (M + 1) + line : line * (M + 1) + e;
-}
-
 // W_M^(j k) for runtime j and compile-time k (warp-uniform j: constant-cache broadcast).
 template <int M>
 __device__ __forceinline__ float2 stage_twiddle(int j, int k) {
   return c_twiddle[((j * k) & (M - 1)) * (256 / M)];
 }
 
-// ---- forward / inverse passes over all M lines of the tile --------------------
+// ---- forward / inverse passes over LINES lines of length M -------------------
+// Element e of line l lives at buf[l * LS + e * ES].  Slot s of a pass maps to
+// (j = s / LINES, line = s % LINES): consecutive lanes take consecutive lines.
 
-template <int M, bool COL, int NT>
-__device__ __forceinline__ void pass_a_fwd(float2* buf, int tid) {
+template <int M, int LINES, int LS, int ES, int NT>
+__device__ __forceinline__ void gpass_a_fwd(float2* buf, int tid) {
   constexpr int N1 = FftPlan<M>::N1, N2 = FftPlan<M>::N2;
-  for (int s = tid; s < M * N1; s += NT) {
-    const int j = s / M, line = s % M;
+  for (int s = tid; s < LINES * N1; s += NT) {
+    const int j = s / LINES, line = s % LINES;
+    float2* p = buf + line * LS + j * ES;
     float2 v[N2];
 #pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) v[n2] = buf[tile_addr<M, COL>(line, j + N1 * n2)];
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = p[N1 * n2 * ES];
     Dft<N2, false>::run(v);
 #pragma unroll
     for (int k2 = 1; k2 < N2; ++k2) v[k2] = cmul(v[k2], stage_twiddle<M>(j, k2));
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) buf[tile_addr<M, COL>(line, j + N1 * k2)] = v[k2];
+    for (int k2 = 0; k2 < N2; ++k2) p[N1 * k2 * ES] = v[k2];
   }
 }
 
-template <int M, bool COL, int NT>
-__device__ __forceinline__ void pass_a_inv(float2* buf, int tid) {
+template <int M, int LINES, int LS, int ES, int NT>
+__device__ __forceinline__ void gpass_a_inv(float2* buf, int tid) {
   constexpr int N1 = FftPlan<M>::N1, N2 = FftPlan<M>::N2;
-  for (int s = tid; s < M * N1; s += NT) {
-    const int j = s / M, line = s % M;
+  for (int s = tid; s < LINES * N1; s += NT) {
+    const int j = s / LINES, line = s % LINES;
+    float2* p = buf + line * LS + j * ES;
     float2 v[N2];
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) v[k2] = buf[tile_addr<M, COL>(line, j + N1 * k2)];
+    for (int k2 = 0; k2 < N2; ++k2) v[k2] = p[N1 * k2 * ES];
 #pragma unroll
     for (int k2 = 1; k2 < N2; ++k2) v[k2] = cmulc(v[k2], stage_twiddle<M>(j, k2));
     Dft<N2, true>::run(v);
 #pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) buf[tile_addr<M, COL>(line, j + N1 * n2)] = v[n2];
+    for (int n2 = 0; n2 < N2; ++n2) p[N1 * n2 * ES] = v[n2];
   }
+}
+
+template <int M, int LINES, int LS, int ES, int NT, bool INV>
+__device__ __forceinline__ void gpass_b(float2* buf, int tid) {
+  constexpr int N1 = FftPlan<M>::N1, N2 = FftPlan<M>::N2;
+  for (int s = tid; s < LINES * N2; s += NT) {
+    const int k2 = s / LINES, line = s % LINES;
+    float2* p = buf + line * LS + N1 * k2 * ES;
+    float2 v[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) v[i] = p[i * ES];
+    Dft<N1, INV>::run(v);
+#pragma unroll
+    for (int i = 0; i < N1; ++i) p[i * ES] = v[i];
+  }
+}
+
+// Full m x m tile, row stride M + 1: rows (COL = false) or columns (COL = true).
+template <int M, bool COL, int NT>
+__device__ __forceinline__ void pass_a_fwd(float2* buf, int tid) {
+  gpass_a_fwd<M, M, COL ? 1 : M + 1, COL ? M + 1 : 1, NT>(buf, tid);
+}
+
+template <int M, bool COL, int NT>
+__device__ __forceinline__ void pass_a_inv(float2* buf, int tid) {
+  gpass_a_inv<M, M, COL ? 1 : M + 1, COL ? M + 1 : 1, NT>(buf, tid);
 }
 
 template <int M, bool COL, int NT, bool INV>
 __device__ __forceinline__ void pass_b(float2* buf, int tid) {
-  constexpr int N1 = FftPlan<M>::N1, N2 = FftPlan<M>::N2;
-  for (int s = tid; s < M * N2; s += NT) {
-    const int k2 = s / M, line = s % M;
-    float2 v[N1];
-#pragma unroll
-    for (int i = 0; i < N1; ++i) v[i] = buf[tile_addr<M, COL>(line, i + N1 * k2)];
-    Dft<N1, INV>::run(v);
-#pragma unroll
-    for (int i = 0; i < N1; ++i) buf[tile_addr<M, COL>(line, i + N1 * k2)] = v[i];
-  }
+  gpass_b<M, M, COL ? 1 : M + 1, COL ? M + 1 : 1, NT, INV>(buf, tid);
 }
 
 // Forward transform up to (not including) the column pass B, which callers

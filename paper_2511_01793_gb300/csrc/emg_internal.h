@@ -26,6 +26,11 @@ struct PrepArgs {
   const float2* probe;
   int m, levels, prolong;
   float alpha, w_eps;
+  // max|Q|^2 of the probe as float bits: read from mq_read; mq_next is reset
+  // to 0 for the combine that follows to fill (atomicMax).
+  const unsigned* mq_read;
+  unsigned* mq_next;
+  int tile, halo;               // tiled prep: level-0 tile side and halo (px)
   float* wq;                    // [m*m] |Q|^2 + w_eps max|Q|^2 (object-combine weight)
   float* u[kMaxLevels];         // per-level rPIE weight u_l (scratch)
   float* T[kMaxLevels];         // per-level I_h^H |Q_l|^2 (side (m >> l) / 2, scratch)
@@ -61,15 +66,20 @@ struct ApplyArgs {
   const float2* qt;
   const float* mu;
   const float* wq;
-  int tiles_x, tiles_y;         // object tiles of 32 x 32 pixels
+  unsigned* mq_next;            // receives max|Q|^2 of the combined probe (atomicMax, float bits)
+  int tiles_x, tiles_y;         // object tiles of kApplyTile x kApplyTile pixels
 };
 
-constexpr int kApplyTile = 32;
-constexpr int kApplyThreads = 256;
+constexpr int kApplyTile = 16;
+constexpr int kApplyThreads = 256;      // one object pixel per thread
+constexpr int kApplyProbeGroups = 8;    // probe blocks: 32 pixels x 8 position groups
 
 cudaError_t upload_twiddles();
 cudaError_t launch_amp_prep(const float* d, float* amp, int m, int n_pos, cudaStream_t s);
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
+cudaError_t launch_probe_max(const float2* probe, int m, unsigned* slot, cudaStream_t s);
+// Fills tile/halo of a and returns true when the tiled prep fits in shared memory.
+bool prep_tiled_config(PrepArgs& a);
 cudaError_t launch_step(int m, int b, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
 cudaError_t launch_misfit(int m, const float2* object, const float2* probe, const int32_t* pos,

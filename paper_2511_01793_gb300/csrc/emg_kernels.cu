@@ -10,6 +10,7 @@
 //   k_misfit<M>    Phi_k = 1/2 ||Q . P_k z - R_k||^2 (Eq. exit_misfit), per position
 //   k_simulate<M>  d_k = |F(Q . P_k z)|^2 (Sec. 2.1 data model)
 //   k_fft2<M>      batched 2-D DFT of natural-order tiles
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "emg_fft.cuh"
@@ -131,6 +132,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const PrepArgs a) {
   float mx = 0.f;
   for (int p = tid; p < m * m; p += kPrepThreads) mx = fmaxf(mx, cabs2(a.probe[p]));
   const float MQ = block_max<kPrepThreads>(mx, redf);
+  if (tid == 0 && a.mq_next) *a.mq_next = 0u;
 
   // level 0: u_0 = alpha (M_Q - |Q|^2), G_0, combine weight
   for (int p = tid; p < m * m; p += kPrepThreads) {
@@ -183,6 +185,166 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const PrepArgs a) {
     }
   }
 }
+
+// max|Q|^2 into *slot (float bits, atomicMax; the slot starts at 0).
+__device__ __forceinline__ void warp_atomic_max(unsigned* slot, float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(slot, __float_as_uint(v));
+}
+
+__global__ void __launch_bounds__(256) k_probe_max(const float2* __restrict__ probe, int n,
+                                                   unsigned* __restrict__ slot) {
+  float mx = 0.f;
+  for (int p = blockIdx.x * 256 + threadIdx.x; p < n; p += gridDim.x * 256) mx = fmaxf(mx, cabs2(probe[p]));
+  warp_atomic_max(slot, mx);
+}
+
+// Tiled probe-only prep: one CTA per tile x tile block of level-0 pixels.
+// The CTA rebuilds the restriction pyramid of its tile plus a halo of
+// 2^(L-1) px (bilinear prolongation reads one coarse neighbour per level) in
+// shared memory and writes the level arrays of its own pixels.
+constexpr int kPrepTileThreads = 256;
+
+struct PrepRegion {
+  int lo_r, lo_c, h, w;   // region of one level, in that level's pixels
+};
+
+__device__ __forceinline__ PrepRegion prep_region(int m, int R0, int C0, int tile, int halo, int l) {
+  PrepRegion g;
+  const int lr = max(0, R0 - halo), hr = min(m, R0 + tile + halo);
+  const int lc = max(0, C0 - halo), hc = min(m, C0 + tile + halo);
+  g.lo_r = lr >> l;
+  g.lo_c = lc >> l;
+  g.h = (hr >> l) - g.lo_r;
+  g.w = (hc >> l) - g.lo_c;
+  return g;
+}
+
+// Prolongation at level-l pixel (r, c) from a coarse array stored on a region
+// (row stride g.w, origin g.lo_r, g.lo_c); mc = full coarse side for clamping.
+template <typename T>
+__device__ __forceinline__ T prolong_region(const T* y, const PrepRegion& g, int mc, int r, int c, int kind) {
+  const int i = r >> 1, j = c >> 1;
+  const T v = y[(i - g.lo_r) * g.w + (j - g.lo_c)];
+  if (kind == 0) return v;
+  const int i2 = (r & 1) ? min(i + 1, mc - 1) : max(i - 1, 0);
+  const int j2 = (c & 1) ? min(j + 1, mc - 1) : max(j - 1, 0);
+  return lerp4<T>(v, y[(i2 - g.lo_r) * g.w + (j - g.lo_c)], y[(i - g.lo_r) * g.w + (j2 - g.lo_c)],
+                  y[(i2 - g.lo_r) * g.w + (j2 - g.lo_c)]);
+}
+
+__global__ void __launch_bounds__(kPrepTileThreads) k_prep_tile(const PrepArgs a) {
+  extern __shared__ float2 smp[];
+  const int tid = threadIdx.x;
+  const int m = a.m, L = a.levels, tile = a.tile, halo = a.halo;
+  const int tiles_per_row = m / tile;
+  const int R0 = (blockIdx.x / tiles_per_row) * tile, C0 = (blockIdx.x % tiles_per_row) * tile;
+  const float MQ = __uint_as_float(*a.mq_read);
+  if (blockIdx.x == 0 && tid == 0) *a.mq_next = 0u;
+
+  // carve shared memory: per level Q_l (float2), u_l (float), T_l (float, level l+1 region)
+  float2* Qs[kMaxLevels];
+  float* us[kMaxLevels];
+  float* Ts[kMaxLevels];
+  {
+    char* base = (char*)smp;
+    size_t off = 0;
+    for (int l = 0; l < L; ++l) {
+      const PrepRegion g = prep_region(m, R0, C0, tile, halo, l);
+      Qs[l] = (float2*)(base + off);
+      off += (size_t)g.h * g.w * sizeof(float2);
+      us[l] = (float*)(base + off);
+      off += (size_t)g.h * g.w * sizeof(float);
+      if (l + 1 < L) {
+        const PrepRegion gc = prep_region(m, R0, C0, tile, halo, l + 1);
+        Ts[l] = (float*)(base + off);
+        off += (size_t)gc.h * gc.w * sizeof(float);
+      }
+      off = (off + 15) & ~(size_t)15;
+    }
+  }
+  // level 0
+  {
+    const PrepRegion g = prep_region(m, R0, C0, tile, halo, 0);
+    for (int p = tid; p < g.h * g.w; p += kPrepTileThreads) {
+      const int r = g.lo_r + p / g.w, c = g.lo_c + p % g.w;
+      const float2 q = a.probe[r * m + c];
+      const float a2 = cabs2(q);
+      const float u = a.alpha * (MQ - a2);
+      Qs[0][p] = q;
+      us[0][p] = u;
+      if (r >= R0 && r < R0 + tile && c >= C0 && c < C0 + tile) {
+        a.G[0][r * m + c] = safe_cdiv(cconj(q), u + a2);
+        a.wq[r * m + c] = fmaf(a.w_eps, MQ, a2);
+      }
+    }
+  }
+  for (int l = 0; l + 1 < L; ++l) {
+    __syncthreads();
+    const PrepRegion gf = prep_region(m, R0, C0, tile, halo, l);
+    const PrepRegion gc = prep_region(m, R0, C0, tile, halo, l + 1);
+    const int mf = m >> l, mc = mf >> 1;
+    const int tr0 = R0 >> (l + 1), tc0 = C0 >> (l + 1), tsz = tile >> (l + 1);
+    // coarse: T = I_h^H |Q_l|^2, Q_{l+1} = I_h^H Q_l, u_{l+1} = W_u^H I_h^H u_l, G_{l+1}
+    for (int p = tid; p < gc.h * gc.w; p += kPrepTileThreads) {
+      const int i = p / gc.w, j = p % gc.w;
+      float t = 0.f, ur = 0.f;
+      float2 qs = czero();
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+          const int pf = (2 * i + dy) * gf.w + 2 * j + dx;
+          const float2 q = Qs[l][pf];
+          t += cabs2(q);
+          qs = cadd(qs, q);
+          ur += us[l][pf];
+        }
+      t *= 0.25f;
+      ur *= 0.25f;
+      qs = cscale(qs, 0.25f);
+      const float aH = cabs2(qs);
+      const float uH = safe_div(aH, t) * ur;
+      Ts[l][p] = t;
+      Qs[l + 1][p] = qs;
+      us[l + 1][p] = uH;
+      const int gi = gc.lo_r + i, gj = gc.lo_c + j;
+      if (gi >= tr0 && gi < tr0 + tsz && gj >= tc0 && gj < tc0 + tsz) {
+        a.Q[l + 1][gi * mc + gj] = qs;
+        a.G[l + 1][gi * mc + gj] = safe_cdiv(cconj(qs), uH + aH);
+      }
+    }
+    __syncthreads();
+    // fine weights of the tile's level-l pixels: W_z = |Q_l|^2 / S, W_R = (I_H^h Q_{l+1}) conj(Q_l) / S
+    const int fr0 = R0 >> l, fc0 = C0 >> l, fsz = tile >> l;
+    for (int p = tid; p < fsz * fsz; p += kPrepTileThreads) {
+      const int r = fr0 + p / fsz, c = fc0 + p % fsz;
+      const float S = prolong_region<float>(Ts[l], gc, mc, r, c, a.prolong);
+      const float2 pq = prolong_region<float2>(Qs[l + 1], gc, mc, r, c, a.prolong);
+      const float2 q = Qs[l][(r - gf.lo_r) * gf.w + (c - gf.lo_c)];
+      a.Wz[l][r * mf + c] = safe_div(cabs2(q), S);
+      a.WR[l][r * mf + c] = safe_cdiv(cmulc(pq, q), S);
+    }
+  }
+}
+
+__host__ size_t prep_tile_smem(const PrepArgs& a) {
+  // worst-case region sizes over tiles (interior tile)
+  size_t bytes = 0;
+  for (int l = 0; l < a.levels; ++l) {
+    const int side = min(a.m, a.tile + 2 * a.halo) >> l;
+    bytes += (size_t)side * side * (sizeof(float2) + sizeof(float));
+    if (l + 1 < a.levels) {
+      const int sc = min(a.m, a.tile + 2 * a.halo) >> (l + 1);
+      bytes += (size_t)sc * sc * sizeof(float);
+    }
+    bytes = (bytes + 15) & ~(size_t)15;
+  }
+  return bytes;
+}
+
+constexpr size_t kPrepTileSmemMax = 96 * 1024;
 
 // ---------------------------------------------------------------------------
 // One scan position per CTA.
@@ -390,15 +552,302 @@ __global__ void __launch_bounds__(StepThreads<M>::value) k_step(const StepArgs a
 }
 
 // ---------------------------------------------------------------------------
-// a8 + a9: deterministic combine.  Blocks [0, tiles) own 32 x 32 object tiles;
-// the remaining blocks own 256 probe pixels each.
+// One scan position per cluster of two CTAs (m = 64, 128).
+//
+// CTA `rank` owns patch rows [rank m/2, (rank+1) m/2) for the gather, the row
+// FFT passes, the multigrid passes and the update, and storage columns
+// [rank m/2, (rank+1) m/2) for the column FFT passes and the modulus
+// replacement.  The two transposes between row and column slabs go through
+// distributed shared memory; the multigrid up-pass reads the one coarse row
+// it needs from the peer (bilinear prolongation).  Per CTA the shared memory
+// is one row slab and one column slab (half of the single-CTA footprint), so
+// a minibatch of B positions occupies 2B SMs.
+namespace cg = cooperative_groups;
+
+template <int M> struct Step2Threads;
+template <> struct Step2Threads<64> { static constexpr int value = 256; };
+template <> struct Step2Threads<128> { static constexpr int value = 512; };
+
+template <int M>
+__host__ __device__ constexpr size_t step2_smem_elems() {
+  return (size_t)(M / 2) * (M + 1) + (size_t)M * (M / 2 + 1);
+}
+
+// Value (gi, j) of a coarse array split by rows between the two CTAs: rows
+// [0, hc) on rank 0, [hc, 2 hc) on rank 1, row stride sc in each.
+template <typename T>
+__device__ __forceinline__ T dist_at(const T* loc, const T* rem, int rank, int hc, int sc, int gi, int j) {
+  const int owner = gi >= hc;
+  const T* base = owner == rank ? loc : rem;
+  return base[(gi - owner * hc) * sc + j];
+}
+
+// (I_H^h y)(r, c) at global level pixel (r, c) for a row-split coarse array of side mc.
+template <typename T>
+__device__ __forceinline__ T prolong_dist(const T* loc, const T* rem, int rank, int mc, int sc, int r, int c,
+                                          int kind) {
+  const int hc = mc >> 1;
+  const int i = r >> 1, j = c >> 1;
+  const T v = dist_at(loc, rem, rank, hc, sc, i, j);
+  if (kind == 0) return v;
+  const int i2 = (r & 1) ? min(i + 1, mc - 1) : max(i - 1, 0);
+  const int j2 = (c & 1) ? min(j + 1, mc - 1) : max(j - 1, 0);
+  return lerp4<T>(v, dist_at(loc, rem, rank, hc, sc, i2, j), dist_at(loc, rem, rank, hc, sc, i, j2),
+                  dist_at(loc, rem, rank, hc, sc, i2, j2));
+}
+
+template <int M>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::value)
+    k_step2(const StepArgs a) {
+  constexpr int NT = Step2Threads<M>::value;
+  constexpr int H = M / 2, SR = M + 1, SC = H + 1;
+  constexpr int N1 = FftPlan<M>::N1, N2 = FftPlan<M>::N2;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int peer = rank ^ 1;
+  extern __shared__ float2 sm[];
+  float2* rowbuf = sm;            // H x SR: my patch rows
+  float2* colbuf = sm + H * SR;   // M x SC: my storage columns (all rows); multigrid buffers later
+  __shared__ float xf[2];
+  __shared__ double xd[2], xd2[2];
+  __shared__ double redd[NT / 32];
+  __shared__ float redf[NT / 32];
+  const int tid = threadIdx.x;
+  const int kb = blockIdx.x >> 1;
+  const int k = a.order[kb];
+  const int o_r = a.pos[2 * k], o_c = a.pos[2 * k + 1];
+  const int row0 = rank * H;
+  float2* peer_col = cl.map_shared_rank(colbuf, peer);
+  float2* peer_row = cl.map_shared_rank(rowbuf, peer);
+  cl.sync();  // both CTAs resident before any distributed shared memory access
+
+  // a1: gather my rows, psi = Q z_k, partial mu_k
+  float mu_l = 0.f;
+  for (int p = tid; p < H * M; p += NT) {
+    const int lr = p / M, c = p % M, r = row0 + lr;
+    const float2 zk = gather_obj(a.object, a.n_rows, a.n_cols, o_r + r, o_c + c);
+    rowbuf[lr * SR + c] = cmul(a.probe[r * M + c], zk);
+    mu_l = fmaxf(mu_l, cabs2(zk));
+  }
+  const float mu_part = block_max<NT>(mu_l, redf);
+  // a2: row passes on my rows
+  gpass_a_fwd<M, H, SR, 1, NT>(rowbuf, tid);
+  __syncthreads();
+  gpass_b<M, H, SR, 1, NT, false>(rowbuf, tid);
+  __syncthreads();
+  // transpose 1: my rows x all storage columns -> column slabs
+  for (int s = tid; s < H * M; s += NT) {
+    const int lr = s / M, e = s % M;
+    float2* dst = (e / H) == rank ? colbuf : peer_col;
+    dst[(row0 + lr) * SC + (e % H)] = rowbuf[lr * SR + e];
+  }
+  if (tid == 0) {
+    xf[rank] = mu_part;
+    *cl.map_shared_rank(&xf[rank], peer) = mu_part;
+  }
+  cl.sync();
+  const float mu = fmaxf(xf[0], xf[1]);
+
+  // a2 (columns) + a3 + a4 (columns) on my storage columns
+  gpass_a_fwd<M, H, 1, SC, NT>(colbuf, tid);
+  __syncthreads();
+  const float* amp = a.amp + (size_t)k * M * M + rank * H;
+  const float inv_m2 = 1.f / (float)(M * M);
+  float acc = 0.f;
+  for (int s = tid; s < H * N2; s += NT) {
+    const int k2 = s / H, lc = s % H;
+    float2 v[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) v[i] = colbuf[(i + N1 * k2) * SC + lc];
+    Dft<N1, false>::run(v);
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      const float am = amp[(i + N1 * k2) * M + lc];
+      const float p2 = cabs2(v[i]);
+      if (p2 > 0.f) {
+        const float inv = rsqrtf(p2);
+        const float dm = fmaf(p2, inv, -am);
+        acc = fmaf(dm, dm, acc);
+        v[i] = cscale(v[i], am * inv * inv_m2);
+      } else {
+        acc = fmaf(am, am, acc);
+        v[i] = make_float2(am * inv_m2, 0.f);
+      }
+    }
+    Dft<N1, true>::run(v);
+#pragma unroll
+    for (int i = 0; i < N1; ++i) colbuf[(i + N1 * k2) * SC + lc] = v[i];
+  }
+  __syncthreads();
+  gpass_a_inv<M, H, 1, SC, NT>(colbuf, tid);
+  const double phi_part = block_sum<NT>((double)acc, redd);  // includes the barrier after the pass
+  // transpose 2: all rows x my columns -> row slabs
+  for (int s = tid; s < M * H; s += NT) {
+    const int r = s / H, lc = s % H;
+    float2* dst = (r / H) == rank ? rowbuf : peer_row;
+    dst[(r % H) * SR + rank * H + lc] = colbuf[r * SC + lc];
+  }
+  if (tid == 0) {
+    xd[rank] = phi_part;
+    *cl.map_shared_rank(&xd[rank], peer) = phi_part;
+  }
+  cl.sync();
+  // a4: inverse row passes -> R (natural order) on my rows
+  gpass_b<M, H, SR, 1, NT, true>(rowbuf, tid);
+  __syncthreads();
+  gpass_a_inv<M, H, SR, 1, NT>(rowbuf, tid);
+  __syncthreads();
+
+  // a5: MAGPIE multigrid on row slabs; level-l buffers (l >= 1) reuse colbuf
+  float2* Zl[kMaxLevels];
+  float2* Rl[kMaxLevels];
+  {
+    size_t off = 0;
+    for (int l = 1; l < a.levels; ++l) {
+      const int wl = M >> l, hl = wl >> 1;
+      Zl[l] = colbuf + off;
+      off += (size_t)hl * (wl + 1);
+      Rl[l] = colbuf + off;
+      off += (size_t)hl * (wl + 1);
+    }
+  }
+  const bool remote_halo = a.prolong != 0;
+  if (a.levels > 1) {
+    {  // restrict level 0 -> 1: z_1 = I_h^H (W_z z_k), R_1 = I_h^H (W_R R)
+      constexpr int wc = M / 2, hc = wc / 2, sc = wc + 1;
+      const float* Wz = a.lv.Wz[0];
+      const float2* WR = a.lv.WR[0];
+      for (int p = tid; p < hc * wc; p += NT) {
+        const int i = p / wc, j = p % wc;
+        float2 zs = czero(), rs = czero();
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            const int lr = 2 * i + dy, r = row0 + lr, c = 2 * j + dx;
+            const float2 zk = gather_obj(a.object, a.n_rows, a.n_cols, o_r + r, o_c + c);
+            zs = cadd(zs, cscale(zk, Wz[r * M + c]));
+            rs = cadd(rs, cmul(WR[r * M + c], rowbuf[lr * SR + c]));
+          }
+        Zl[1][i * sc + j] = cscale(zs, 0.25f);
+        Rl[1][i * sc + j] = cscale(rs, 0.25f);
+      }
+    }
+    __syncthreads();
+    for (int l = 1; l + 1 < a.levels; ++l) {
+      const int wf = M >> l, sf = wf + 1, hf = wf >> 1, wc = wf >> 1, hc = wc >> 1, sc = wc + 1;
+      const float* Wz = a.lv.Wz[l];
+      const float2* WR = a.lv.WR[l];
+      for (int p = tid; p < hc * wc; p += NT) {
+        const int i = p / wc, j = p % wc;
+        float2 zs = czero(), rs = czero();
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            const int lr = 2 * i + dy, r = rank * hf + lr, c = 2 * j + dx;
+            zs = cadd(zs, cscale(Zl[l][lr * sf + c], Wz[r * wf + c]));
+            rs = cadd(rs, cmul(WR[r * wf + c], Rl[l][lr * sf + c]));
+          }
+        Zl[l + 1][i * sc + j] = cscale(zs, 0.25f);
+        Rl[l + 1][i * sc + j] = cscale(rs, 0.25f);
+      }
+      __syncthreads();
+    }
+    {  // coarsest level: correction c = G (R - Q z), stored over z
+      const int l = a.levels - 1;
+      const int wl = M >> l, hl = wl >> 1, sl = wl + 1;
+      const float2* G = a.lv.G[l];
+      const float2* Q = a.lv.Q[l];
+      for (int p = tid; p < hl * wl; p += NT) {
+        const int i = p / wl, j = p % wl, gi = rank * hl + i;
+        const float2 z = Zl[l][i * sl + j];
+        Zl[l][i * sl + j] = cmul(G[gi * wl + j], csub(Rl[l][i * sl + j], cmul(Q[gi * wl + j], z)));
+      }
+    }
+    // back up: c_l = I_H^h c_{l+1} + G_l (R_l - Q_l (z_l + I_H^h c_{l+1}))
+    for (int l = a.levels - 2; l >= 1; --l) {
+      if (remote_halo) cl.sync(); else __syncthreads();
+      const int wl = M >> l, hl = wl >> 1, sl = wl + 1, wc = wl >> 1, sc = wc + 1;
+      const float2* G = a.lv.G[l];
+      const float2* Q = a.lv.Q[l];
+      const float2* Zc = Zl[l + 1];
+      const float2* Zc_peer = cl.map_shared_rank(Zl[l + 1], peer);
+      for (int p = tid; p < hl * wl; p += NT) {
+        const int i = p / wl, j = p % wl, gi = rank * hl + i;
+        const float2 pro = prolong_dist<float2>(Zc, Zc_peer, rank, wc, sc, gi, j, a.prolong);
+        const float2 zp = cadd(Zl[l][i * sl + j], pro);
+        Zl[l][i * sl + j] = cadd(pro, cmul(G[gi * wl + j], csub(Rl[l][i * sl + j], cmul(Q[gi * wl + j], zp))));
+      }
+    }
+    if (remote_halo) cl.sync(); else __syncthreads();
+  }
+
+  // a5 (finest level) + a6 + a7
+  const float inv_mu = mu > 0.f ? 1.f / mu : 0.f;
+  const float2* G0 = a.lv.G[0];
+  float2* zt = a.zt + (size_t)kb * M * M;
+  float2* qt = a.qt + (size_t)kb * M * M;
+  const float2* Z1 = Zl[1];
+  const float2* Z1_peer = a.levels > 1 ? cl.map_shared_rank(Zl[1], peer) : nullptr;
+  float acc_after = 0.f;
+  for (int p = tid; p < H * M; p += NT) {
+    const int lr = p / M, c = p % M, r = row0 + lr;
+    const float2 zk = gather_obj(a.object, a.n_rows, a.n_cols, o_r + r, o_c + c);
+    const float2 q = a.probe[r * M + c];
+    const float2 R = rowbuf[lr * SR + c];
+    const float2 res = csub(R, cmul(q, zk));
+    float2 zplus;
+    if (a.levels == 1) {
+      zplus = cadd(zk, cmul(G0[r * M + c], res));
+    } else {
+      const float2 pro = prolong_dist<float2>(Z1, Z1_peer, rank, M / 2, M / 2 + 1, r, c, a.prolong);
+      const float2 zp = cadd(zk, pro);
+      zplus = cadd(zp, cmul(G0[r * M + c], csub(R, cmul(q, zp))));
+    }
+    const float2 qplus = cadd(q, cscale(cconjmul(zk, res), inv_mu));
+    float2 zn, qn;
+    if (a.joint) {
+      zn = geometric_mean_aligned(zk, zplus);
+      qn = geometric_mean_aligned(q, qplus);
+    } else {
+      zn = zplus;
+      qn = qplus;
+    }
+    zt[r * M + c] = zn;
+    qt[r * M + c] = qn;
+    if (a.verify) acc_after += cabs2(csub(cmul(qn, zn), R));
+  }
+  if (a.verify) {
+    const double part = 0.5 * block_sum<NT>((double)acc_after, redd);
+    if (tid == 0) {
+      xd2[rank] = part;
+      *cl.map_shared_rank(&xd2[rank], peer) = part;
+    }
+  }
+  cl.sync();  // the peer may still read my coarse rows; also publishes xd2
+  if (rank == 0 && tid == 0) {
+    a.mu[kb] = mu;
+    a.phi[kb] = (xd[0] + xd[1]) * (0.5 / (double)(M * M));
+    if (a.verify) a.phi_after[kb] = xd2[0] + xd2[1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a8 + a9: deterministic combine.  Blocks [0, tiles) own 16 x 16 object tiles
+// (one pixel per thread); the remaining blocks own 32 probe pixels each, with
+// 8 thread groups summing disjoint position subsets that are then added in a
+// fixed order.  The new probe's max|Q|^2 goes to a.mq_next for the next prep.
 __global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
   extern __shared__ int list[];  // [b][3] = (kb, row, col) of patches overlapping the tile
   __shared__ int warp_count[kApplyThreads / 32];
   __shared__ int total;
+  __shared__ float2 part_s[kApplyProbeGroups][32];
+  __shared__ int part_n[kApplyProbeGroups][32];
   const int tid = threadIdx.x;
   const int n_tiles = a.tiles_x * a.tiles_y;
   const int m = a.m;
+  const size_t mm = (size_t)m * m;
   if ((int)blockIdx.x < n_tiles) {
     const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x % a.tiles_x;
     const int r0 = ty * kApplyTile, c0 = tx * kApplyTile;
@@ -436,56 +885,69 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
       __syncthreads();
     }
     const int cnt = total;
-    if (cnt == 0) return;
-    for (int p = tid; p < kApplyTile * kApplyTile; p += kApplyThreads) {
-      const int row = r0 + p / kApplyTile, col = c0 + p % kApplyTile;
-      if (row >= a.n_rows || col >= a.n_cols) continue;
-      float2 num = czero();
-      float den = 0.f;
-      bool covered = false;
-      for (int t = 0; t < cnt; ++t) {
-        const int lr = row - list[3 * t + 1], lc = col - list[3 * t + 2];
-        if ((unsigned)lr < (unsigned)m && (unsigned)lc < (unsigned)m) {
-          const int kb = list[3 * t];
-          const float2 v = a.zt[(size_t)kb * m * m + lr * m + lc];
-          covered = true;
-          if (a.combine == 0) {
-            const float w = a.wq[lr * m + lc];
-            num = make_float2(fmaf(w, v.x, num.x), fmaf(w, v.y, num.y));
-            den += w;
-          } else {
-            num = cadd(num, v);
-            den += 1.f;
-          }
+    const int row = r0 + tid / kApplyTile, col = c0 + tid % kApplyTile;
+    if (cnt == 0 || row >= a.n_rows || col >= a.n_cols) return;
+    float2 num = czero();
+    float den = 0.f;
+    bool covered = false;
+    for (int t = 0; t < cnt; ++t) {
+      const int lr = row - list[3 * t + 1], lc = col - list[3 * t + 2];
+      if ((unsigned)lr < (unsigned)m && (unsigned)lc < (unsigned)m) {
+        const int kb = list[3 * t];
+        const float2 v = a.zt[(size_t)kb * mm + lr * m + lc];
+        covered = true;
+        if (a.combine == 0) {
+          const float w = a.wq[lr * m + lc];
+          num = make_float2(fmaf(w, v.x, num.x), fmaf(w, v.y, num.y));
+          den += w;
+        } else {
+          num = cadd(num, v);
+          den += 1.f;
         }
       }
-      if (!covered) continue;
-      const size_t gi = (size_t)row * a.n_cols + col;
-      if (a.combine == 0) {
-        a.object[gi] = safe_cdiv(num, den);
-      } else {
-        const float2 z = a.object[gi];
-        a.object[gi] = cadd(z, csub(num, cscale(z, den)));
-      }
+    }
+    if (!covered) return;
+    const size_t gi = (size_t)row * a.n_cols + col;
+    if (a.combine == 0) {
+      a.object[gi] = safe_cdiv(num, den);
+    } else {
+      const float2 z = a.object[gi];
+      a.object[gi] = cadd(z, csub(num, cscale(z, den)));
     }
   } else {
-    const int p = (blockIdx.x - n_tiles) * kApplyThreads + tid;
-    if (p >= m * m) return;
+    const int lane = tid & 31, g = tid >> 5;
+    const int p = (blockIdx.x - n_tiles) * 32 + lane;
     float2 s = czero();
     int cnt = 0;
-    for (int kb = 0; kb < a.b; ++kb) {
-      if (a.mu[kb] > 0.f) {
-        s = cadd(s, a.qt[(size_t)kb * m * m + p]);
-        ++cnt;
+    if (p < (int)mm) {
+      for (int kb = g; kb < a.b; kb += kApplyProbeGroups) {
+        if (a.mu[kb] > 0.f) {
+          s = cadd(s, a.qt[(size_t)kb * mm + p]);
+          ++cnt;
+        }
       }
     }
-    if (cnt == 0) return;
-    if (a.combine == 0) {
-      a.probe[p] = cscale(s, 1.f / (float)cnt);
-    } else {
-      const float2 q = a.probe[p];
-      a.probe[p] = cadd(q, csub(s, cscale(q, (float)cnt)));
+    part_s[g][lane] = s;
+    part_n[g][lane] = cnt;
+    __syncthreads();
+    if (g != 0) return;
+    float a2 = 0.f;
+    if (p < (int)mm) {
+      float2 tot = part_s[0][lane];
+      int n = part_n[0][lane];
+#pragma unroll
+      for (int i = 1; i < kApplyProbeGroups; ++i) {
+        tot = cadd(tot, part_s[i][lane]);
+        n += part_n[i][lane];
+      }
+      float2 q = a.probe[p];
+      if (n > 0) {
+        q = (a.combine == 0) ? cscale(tot, 1.f / (float)n) : cadd(q, csub(tot, cscale(q, (float)n)));
+        a.probe[p] = q;
+      }
+      a2 = cabs2(q);
     }
+    if (a.mq_next) warp_atomic_max(a.mq_next, a2);
   }
 }
 
@@ -721,11 +1183,19 @@ cudaError_t upload_twiddles() {
   if ((e = set_step_smem<32>()) != cudaSuccess) return e;
   if ((e = set_step_smem<64>()) != cudaSuccess) return e;
   if ((e = set_step_smem<128>()) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_step2<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(step2_smem_elems<64>() * sizeof(float2)))) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_step2<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(step2_smem_elems<128>() * sizeof(float2)))) != cudaSuccess)
+    return e;
   if ((e = set_aux_smem<16>()) != cudaSuccess) return e;
   if ((e = set_aux_smem<32>()) != cudaSuccess) return e;
   if ((e = set_aux_smem<64>()) != cudaSuccess) return e;
   if ((e = set_aux_smem<128>()) != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_prep_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepTileSmemMax);
   return e;
 }
 
@@ -743,18 +1213,50 @@ cudaError_t launch_amp_prep(const float* d, float* amp, int m, int n_pos, cudaSt
   return cudaGetLastError();
 }
 
+bool prep_tiled_config(PrepArgs& a) {
+  int tile = 32;
+  while (tile < (1 << (a.levels - 1))) tile *= 2;
+  if (tile > a.m) tile = a.m;
+  a.tile = tile;
+  a.halo = (a.prolong == 1) ? (1 << (a.levels - 1)) : 0;
+  if ((tile >> (a.levels - 1)) < 1) return false;
+  return prep_tile_smem(a) <= kPrepTileSmemMax;
+}
+
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
-  k_prep<<<1, kPrepThreads, 0, s>>>(a);
+  PrepArgs t = a;
+  if (a.mq_read && prep_tiled_config(t)) {
+    const int tiles = (t.m / t.tile) * (t.m / t.tile);
+    k_prep_tile<<<tiles, kPrepTileThreads, prep_tile_smem(t), s>>>(t);
+  } else {
+    k_prep<<<1, kPrepThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_max(const float2* probe, int m, unsigned* slot, cudaStream_t s) {
+  const int n = m * m;
+  int blocks = (n + 255) / 256;
+  if (blocks > 64) blocks = 64;
+  k_probe_max<<<blocks, 256, 0, s>>>(probe, n, slot);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_step2_t(int b, const StepArgs& a, cudaStream_t s) {
+  k_step2<M><<<2 * b, Step2Threads<M>::value, step2_smem_elems<M>() * sizeof(float2), s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_step(int m, int b, const StepArgs& a, cudaStream_t s) {
+  if (m == 128) return launch_step2_t<128>(b, a, s);
+  if (m == 64) return launch_step2_t<64>(b, a, s);
   EMG_DISPATCH_M(m, (launch_step_t<M>(b, a, s)));
 }
 
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
   const int n_tiles = a.tiles_x * a.tiles_y;
-  const int n_probe = (a.m * a.m + kApplyThreads - 1) / kApplyThreads;
+  const int n_probe = (a.m * a.m + 31) / 32;
   const size_t bytes = (size_t)a.b * 3 * sizeof(int);
   k_apply<<<n_tiles + n_probe, kApplyThreads, bytes, s>>>(a);
   return cudaGetLastError();
@@ -818,7 +1320,7 @@ std::mutex g_noalloc_mu;
 unsigned char* g_noalloc_base[256] = {nullptr};
 
 struct NoAllocLayout {
-  size_t idx, wq, zt, qt, mu, phi, phi_after, total;
+  size_t idx, mq, wq, zt, qt, mu, phi, phi_after, total;
   size_t G[kMaxLevels], Q[kMaxLevels], u[kMaxLevels], Wz[kMaxLevels], WR[kMaxLevels], T[kMaxLevels];
 };
 
@@ -832,6 +1334,7 @@ NoAllocLayout noalloc_layout(int m, int levels, int b) {
     return off;
   };
   L.idx = take((size_t)b * sizeof(int32_t));
+  L.mq = take(2 * sizeof(unsigned));
   for (int l = 0; l < levels; ++l) {
     const size_t n = (size_t)(m >> l) * (m >> l);
     L.G[l] = take(n * sizeof(float2));
@@ -919,9 +1422,15 @@ extern "C" emg_status emg_step_minibatch_noalloc(float* object, int32_t n_rows, 
   if (cudaMemcpyAsync(d_idx, idx, (size_t)b * sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return EMG_ECUDA;
 
+  unsigned* d_mq = (unsigned*)(base + L.mq);
+  if (cudaMemsetAsync(d_mq, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return EMG_ECUDA;
+  if (launch_probe_max((const float2*)probe, m, d_mq, s) != cudaSuccess) return EMG_ECUDA;
+
   PrepArgs pa{};
   StepArgs sa{};
   pa.probe = (const float2*)probe;
+  pa.mq_read = d_mq;
+  pa.mq_next = d_mq + 1;
   pa.m = m;
   pa.levels = p->levels;
   pa.prolong = p->prolong;
@@ -972,6 +1481,7 @@ extern "C" emg_status emg_step_minibatch_noalloc(float* object, int32_t n_rows, 
   aa.qt = sa.qt;
   aa.mu = sa.mu;
   aa.wq = pa.wq;
+  aa.mq_next = d_mq + 1;
   aa.tiles_x = (n_cols + kApplyTile - 1) / kApplyTile;
   aa.tiles_y = (n_rows + kApplyTile - 1) / kApplyTile;
 
