@@ -311,12 +311,14 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   sa.pos = c->d_pos;
   sa.amp = c->d_amp;
   sa.order = d_idx;
+  sa.mq = pa.mq_read;
   sa.n_rows = c->n_rows;
   sa.n_cols = c->n_cols;
   sa.levels = c->par.levels;
   sa.prolong = c->par.prolong;
   sa.joint = c->par.joint;
   sa.verify = c->verify;
+  sa.alpha = c->par.alpha;
   sa.lv = c->lv;
   sa.zt = c->d_zt;
   sa.qt = c->d_qt;

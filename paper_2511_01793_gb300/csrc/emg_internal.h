@@ -46,8 +46,10 @@ struct StepArgs {
   const int32_t* pos;
   const float* amp;             // sqrt(max(d,0)) in the FFT's storage order, [N][m][m]
   const int32_t* order;         // positions of this minibatch, [b]
+  const unsigned* mq;           // max|Q|^2 of the probe (float bits), read by the cluster step
   int n_rows, n_cols;
   int levels, prolong, joint, verify;
+  float alpha;                  // rPIE constant (level-0 gain formed in the cluster step)
   LevelArrays lv;
   float2* zt;                   // [b][m*m] joint-step object patches z~_k
   float2* qt;                   // [b][m*m] joint-step probes Q~_k

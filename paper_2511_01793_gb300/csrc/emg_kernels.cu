@@ -57,6 +57,26 @@ __device__ __forceinline__ float2 geometric_mean_aligned(float2 x, float2 xp) {
   return y;
 }
 
+// Principal square root by Kahan's formula with hardware reciprocal square
+// roots (rsqrtf) for |w| and the half-sum: s = (|x| + |w|)/2, t = sqrt(s),
+// root = (t, y/(2t)) for x >= 0 and (|y|/(2t), sign(y) t) otherwise.
+__device__ __forceinline__ float2 csqrt_principal_fast(float2 w) {
+  const float n = fmaf(w.x, w.x, w.y * w.y);
+  if (n == 0.f) return czero();
+  const float mag = n * rsqrtf(n);
+  const float s = 0.5f * (fabsf(w.x) + mag);
+  const float rt = rsqrtf(s);
+  const float t = s * rt, h = 0.5f * rt;
+  if (w.x >= 0.f) return make_float2(t, w.y * h);
+  return make_float2(fabsf(w.y) * h, copysignf(t, w.y));
+}
+
+__device__ __forceinline__ float2 geometric_mean_aligned_fast(float2 x, float2 xp) {
+  float2 y = csqrt_principal_fast(cmul(x, xp));
+  if (fmaf(y.x, x.x, y.y * x.y) < 0.f) y = make_float2(-y.x, -y.y);
+  return y;
+}
+
 template <typename T>
 __device__ __forceinline__ T lerp4(T a, T b, T c, T d);
 template <>
@@ -91,6 +111,25 @@ __device__ __forceinline__ float block_max(float v, float* sh) {
   for (int i = 1; i < NT / 32; ++i) r = fmaxf(r, sh[i]);
   __syncthreads();
   return r;
+}
+
+// Sum over the block of per-thread FP32 partials: FP32 warp trees, then the
+// NT/32 warp sums added in FP64 by one thread in a fixed order; the result is
+// broadcast.  Deterministic; avoids FP64 work in every thread.
+template <int NT>
+__device__ __forceinline__ double block_sum_f(float v, float* shf, double* shd) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) shf[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) r += (double)shf[i];
+    shd[0] = r;
+  }
+  __syncthreads();
+  return shd[0];
 }
 
 template <int NT>
@@ -568,32 +607,22 @@ template <int M> struct Step2Threads;
 template <> struct Step2Threads<64> { static constexpr int value = 256; };
 template <> struct Step2Threads<128> { static constexpr int value = 512; };
 
+// Shared memory of k_step2 in float2: row slab, column slab, object slab z_k.
 template <int M>
 __host__ __device__ constexpr size_t step2_smem_elems() {
-  return (size_t)(M / 2) * (M + 1) + (size_t)M * (M / 2 + 1);
+  return (size_t)(M / 2) * (M + 1) + (size_t)M * (M / 2 + 1) + (size_t)(M / 2) * M;
 }
 
-// Value (gi, j) of a coarse array split by rows between the two CTAs: rows
-// [0, hc) on rank 0, [hc, 2 hc) on rank 1, row stride sc in each.
+// (I_H^h y)(lr, c) for a coarse row slab stored with one halo row above and
+// below (y points at my first row, row stride sl); lr is the local fine row.
 template <typename T>
-__device__ __forceinline__ T dist_at(const T* loc, const T* rem, int rank, int hc, int sc, int gi, int j) {
-  const int owner = gi >= hc;
-  const T* base = owner == rank ? loc : rem;
-  return base[(gi - owner * hc) * sc + j];
-}
-
-// (I_H^h y)(r, c) at global level pixel (r, c) for a row-split coarse array of side mc.
-template <typename T>
-__device__ __forceinline__ T prolong_dist(const T* loc, const T* rem, int rank, int mc, int sc, int r, int c,
-                                          int kind) {
-  const int hc = mc >> 1;
-  const int i = r >> 1, j = c >> 1;
-  const T v = dist_at(loc, rem, rank, hc, sc, i, j);
+__device__ __forceinline__ T prolong_halo(const T* y, int sl, int wc, int lr, int c, int kind) {
+  const int i = lr >> 1, j = c >> 1;
+  const T v = y[i * sl + j];
   if (kind == 0) return v;
-  const int i2 = (r & 1) ? min(i + 1, mc - 1) : max(i - 1, 0);
-  const int j2 = (c & 1) ? min(j + 1, mc - 1) : max(j - 1, 0);
-  return lerp4<T>(v, dist_at(loc, rem, rank, hc, sc, i2, j), dist_at(loc, rem, rank, hc, sc, i, j2),
-                  dist_at(loc, rem, rank, hc, sc, i2, j2));
+  const int i2 = (lr & 1) ? i + 1 : i - 1;
+  const int j2 = (c & 1) ? min(j + 1, wc - 1) : max(j - 1, 0);
+  return lerp4<T>(v, y[i2 * sl + j], y[i * sl + j2], y[i2 * sl + j2]);
 }
 
 template <int M>
@@ -605,12 +634,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int peer = rank ^ 1;
+  constexpr int PER = H * M / NT;          // pixels of my row slab per thread
+  constexpr int SLOTS = H * N2 / NT;       // spectral slots per thread in the column pass B
+  static_assert(H * M % NT == 0 && H * N2 % NT == 0, "thread count must divide the slab");
   extern __shared__ float2 sm[];
-  float2* rowbuf = sm;            // H x SR: my patch rows
-  float2* colbuf = sm + H * SR;   // M x SC: my storage columns (all rows); multigrid buffers later
+  float2* rowbuf = sm;                     // H x SR: my patch rows
+  float2* colbuf = sm + H * SR;            // M x SC: my storage columns (all rows); multigrid buffers later
+  float2* zbuf = colbuf + M * SC;          // H x M: z_k on my rows (gathered once)
   __shared__ float xf[2];
   __shared__ double xd[2], xd2[2];
-  __shared__ double redd[NT / 32];
+  __shared__ double redd[2];
   __shared__ float redf[NT / 32];
   const int tid = threadIdx.x;
   const int kb = blockIdx.x >> 1;
@@ -619,13 +652,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
   const int row0 = rank * H;
   float2* peer_col = cl.map_shared_rank(colbuf, peer);
   float2* peer_row = cl.map_shared_rank(rowbuf, peer);
-  cl.sync();  // both CTAs resident before any distributed shared memory access
+
+  // amplitudes of my spectral slots: issued now, consumed after the row passes
+  const float* amp = a.amp + (size_t)k * M * M + rank * H;
+  float am_reg[SLOTS][N1];
+#pragma unroll
+  for (int t = 0; t < SLOTS; ++t) {
+    const int s = tid + t * NT, k2 = s / H, lc = s % H;
+#pragma unroll
+    for (int i = 0; i < N1; ++i) am_reg[t][i] = __ldg(amp + (i + N1 * k2) * M + lc);
+  }
+  const float MQ = __uint_as_float(*a.mq);
+  cl.barrier_arrive();  // completed (wait) before the first distributed shared memory access
 
   // a1: gather my rows, psi = Q z_k, partial mu_k
   float mu_l = 0.f;
-  for (int p = tid; p < H * M; p += NT) {
+#pragma unroll 4
+  for (int t = 0; t < PER; ++t) {
+    const int p = tid + t * NT;
     const int lr = p / M, c = p % M, r = row0 + lr;
     const float2 zk = gather_obj(a.object, a.n_rows, a.n_cols, o_r + r, o_c + c);
+    zbuf[p] = zk;
     rowbuf[lr * SR + c] = cmul(a.probe[r * M + c], zk);
     mu_l = fmaxf(mu_l, cabs2(zk));
   }
@@ -635,6 +682,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
   __syncthreads();
   gpass_b<M, H, SR, 1, NT, false>(rowbuf, tid);
   __syncthreads();
+  cl.barrier_wait();  // both CTAs resident
   // transpose 1: my rows x all storage columns -> column slabs
   for (int s = tid; s < H * M; s += NT) {
     const int lr = s / M, e = s % M;
@@ -651,18 +699,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
   // a2 (columns) + a3 + a4 (columns) on my storage columns
   gpass_a_fwd<M, H, 1, SC, NT>(colbuf, tid);
   __syncthreads();
-  const float* amp = a.amp + (size_t)k * M * M + rank * H;
   const float inv_m2 = 1.f / (float)(M * M);
   float acc = 0.f;
-  for (int s = tid; s < H * N2; s += NT) {
-    const int k2 = s / H, lc = s % H;
+#pragma unroll
+  for (int t = 0; t < SLOTS; ++t) {
+    const int s = tid + t * NT, k2 = s / H, lc = s % H;
     float2 v[N1];
 #pragma unroll
     for (int i = 0; i < N1; ++i) v[i] = colbuf[(i + N1 * k2) * SC + lc];
     Dft<N1, false>::run(v);
 #pragma unroll
     for (int i = 0; i < N1; ++i) {
-      const float am = amp[(i + N1 * k2) * M + lc];
+      const float am = am_reg[t][i];
       const float p2 = cabs2(v[i]);
       if (p2 > 0.f) {
         const float inv = rsqrtf(p2);
@@ -680,7 +728,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
   }
   __syncthreads();
   gpass_a_inv<M, H, 1, SC, NT>(colbuf, tid);
-  const double phi_part = block_sum<NT>((double)acc, redd);  // includes the barrier after the pass
+  const double phi_part = block_sum_f<NT>(acc, redf, redd);  // includes the barrier after the pass
   // transpose 2: all rows x my columns -> row slabs
   for (int s = tid; s < M * H; s += NT) {
     const int r = s / H, lc = s % H;
@@ -698,20 +746,32 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
   gpass_a_inv<M, H, SR, 1, NT>(rowbuf, tid);
   __syncthreads();
 
-  // a5: MAGPIE multigrid on row slabs; level-l buffers (l >= 1) reuse colbuf
+  // a5: MAGPIE multigrid on row slabs; level-l buffers (l >= 1) reuse colbuf.
+  // Z_l keeps one halo row above and below my rows for the prolongation.
   float2* Zl[kMaxLevels];
   float2* Rl[kMaxLevels];
   {
     size_t off = 0;
     for (int l = 1; l < a.levels; ++l) {
-      const int wl = M >> l, hl = wl >> 1;
-      Zl[l] = colbuf + off;
-      off += (size_t)hl * (wl + 1);
+      const int wl = M >> l, hl = wl >> 1, sl = wl + 1;
+      Zl[l] = colbuf + off + sl;
+      off += (size_t)(hl + 2) * sl;
       Rl[l] = colbuf + off;
-      off += (size_t)hl * (wl + 1);
+      off += (size_t)hl * sl;
     }
   }
-  const bool remote_halo = a.prolong != 0;
+  // Copies the rows of the coarse correction at level l adjacent to my slab
+  // (from the peer, or my own edge row where the patch ends) into the halo.
+  auto fill_halo = [&](int l) {
+    const int wl = M >> l, hl = wl >> 1, sl = wl + 1;
+    float2* Z = Zl[l];
+    const float2* Zp = cl.map_shared_rank(Zl[l], peer);
+    for (int j = tid; j < wl; j += NT) {
+      Z[-sl + j] = rank == 0 ? Z[j] : Zp[(hl - 1) * sl + j];
+      Z[hl * sl + j] = rank == 0 ? Zp[j] : Z[(hl - 1) * sl + j];
+    }
+  };
+  const bool halo = a.prolong != 0;
   if (a.levels > 1) {
     {  // restrict level 0 -> 1: z_1 = I_h^H (W_z z_k), R_1 = I_h^H (W_R R)
       constexpr int wc = M / 2, hc = wc / 2, sc = wc + 1;
@@ -725,7 +785,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
 #pragma unroll
           for (int dx = 0; dx < 2; ++dx) {
             const int lr = 2 * i + dy, r = row0 + lr, c = 2 * j + dx;
-            const float2 zk = gather_obj(a.object, a.n_rows, a.n_cols, o_r + r, o_c + c);
+            const float2 zk = zbuf[lr * M + c];
             zs = cadd(zs, cscale(zk, Wz[r * M + c]));
             rs = cadd(rs, cmul(WR[r * M + c], rowbuf[lr * SR + c]));
           }
@@ -767,49 +827,64 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
     }
     // back up: c_l = I_H^h c_{l+1} + G_l (R_l - Q_l (z_l + I_H^h c_{l+1}))
     for (int l = a.levels - 2; l >= 1; --l) {
-      if (remote_halo) cl.sync(); else __syncthreads();
+      if (halo) {
+        cl.sync();
+        fill_halo(l + 1);
+      }
+      __syncthreads();
       const int wl = M >> l, hl = wl >> 1, sl = wl + 1, wc = wl >> 1, sc = wc + 1;
       const float2* G = a.lv.G[l];
       const float2* Q = a.lv.Q[l];
-      const float2* Zc = Zl[l + 1];
-      const float2* Zc_peer = cl.map_shared_rank(Zl[l + 1], peer);
       for (int p = tid; p < hl * wl; p += NT) {
         const int i = p / wl, j = p % wl, gi = rank * hl + i;
-        const float2 pro = prolong_dist<float2>(Zc, Zc_peer, rank, wc, sc, gi, j, a.prolong);
+        const float2 pro = prolong_halo<float2>(Zl[l + 1], sc, wc, i, j, a.prolong);
         const float2 zp = cadd(Zl[l][i * sl + j], pro);
         Zl[l][i * sl + j] = cadd(pro, cmul(G[gi * wl + j], csub(Rl[l][i * sl + j], cmul(Q[gi * wl + j], zp))));
       }
     }
-    if (remote_halo) cl.sync(); else __syncthreads();
+    if (halo) {
+      cl.sync();
+      fill_halo(1);
+    }
+    __syncthreads();
   }
 
-  // a5 (finest level) + a6 + a7
+  // a5 (finest level) + a6 + a7; the level-0 gain conj(Q)/(u_0 + |Q|^2) is formed here
   const float inv_mu = mu > 0.f ? 1.f / mu : 0.f;
-  const float2* G0 = a.lv.G[0];
   float2* zt = a.zt + (size_t)kb * M * M;
   float2* qt = a.qt + (size_t)kb * M * M;
   const float2* Z1 = Zl[1];
-  const float2* Z1_peer = a.levels > 1 ? cl.map_shared_rank(Zl[1], peer) : nullptr;
   float acc_after = 0.f;
-  for (int p = tid; p < H * M; p += NT) {
+  float2 qv[PER];
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int p = tid + t * NT;
+    qv[t] = __ldg(a.probe + row0 * M + p);
+  }
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int p = tid + t * NT;
     const int lr = p / M, c = p % M, r = row0 + lr;
-    const float2 zk = gather_obj(a.object, a.n_rows, a.n_cols, o_r + r, o_c + c);
-    const float2 q = a.probe[r * M + c];
+    const float2 zk = zbuf[p];
+    const float2 q = qv[t];
     const float2 R = rowbuf[lr * SR + c];
     const float2 res = csub(R, cmul(q, zk));
+    const float a2 = cabs2(q);
+    const float den = fmaf(a.alpha, MQ - a2, a2);
+    const float2 g0 = den != 0.f ? cscale(cconj(q), __frcp_rn(den)) : czero();
     float2 zplus;
     if (a.levels == 1) {
-      zplus = cadd(zk, cmul(G0[r * M + c], res));
+      zplus = cadd(zk, cmul(g0, res));
     } else {
-      const float2 pro = prolong_dist<float2>(Z1, Z1_peer, rank, M / 2, M / 2 + 1, r, c, a.prolong);
+      const float2 pro = prolong_halo<float2>(Z1, M / 2 + 1, M / 2, lr, c, a.prolong);
       const float2 zp = cadd(zk, pro);
-      zplus = cadd(zp, cmul(G0[r * M + c], csub(R, cmul(q, zp))));
+      zplus = cadd(zp, cmul(g0, csub(R, cmul(q, zp))));
     }
     const float2 qplus = cadd(q, cscale(cconjmul(zk, res), inv_mu));
     float2 zn, qn;
     if (a.joint) {
-      zn = geometric_mean_aligned(zk, zplus);
-      qn = geometric_mean_aligned(q, qplus);
+      zn = geometric_mean_aligned_fast(zk, zplus);
+      qn = geometric_mean_aligned_fast(q, qplus);
     } else {
       zn = zplus;
       qn = qplus;
@@ -819,7 +894,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
     if (a.verify) acc_after += cabs2(csub(cmul(qn, zn), R));
   }
   if (a.verify) {
-    const double part = 0.5 * block_sum<NT>((double)acc_after, redd);
+    const double part = 0.5 * block_sum_f<NT>(acc_after, redf, redd);
     if (tid == 0) {
       xd2[rank] = part;
       *cl.map_shared_rank(&xd2[rank], peer) = part;
@@ -1214,7 +1289,7 @@ cudaError_t launch_amp_prep(const float* d, float* amp, int m, int n_pos, cudaSt
 }
 
 bool prep_tiled_config(PrepArgs& a) {
-  int tile = 32;
+  int tile = 16;
   while (tile < (1 << (a.levels - 1))) tile *= 2;
   if (tile > a.m) tile = a.m;
   a.tile = tile;
@@ -1462,6 +1537,8 @@ extern "C" emg_status emg_step_minibatch_noalloc(float* object, int32_t n_rows, 
   sa.prolong = p->prolong;
   sa.joint = p->joint;
   sa.verify = 0;
+  sa.alpha = p->alpha;
+  sa.mq = d_mq;
   sa.zt = (float2*)(base + L.zt);
   sa.qt = (float2*)(base + L.qt);
   sa.mu = (float*)(base + L.mu);
