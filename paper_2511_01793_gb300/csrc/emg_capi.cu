@@ -46,6 +46,15 @@ struct emg_ctx {
   double* d_scalar = nullptr;     // [64] assorted scalar results
   double* d_norm = nullptr;       // [1024] normalisation partials
   unsigned* d_mq = nullptr;       // [2] max|Q|^2 slots (float bits), alternating per minibatch
+  int32_t* d_epoch_order = nullptr;  // [N] order read by the captured epoch graph
+
+  // One epoch captured as a CUDA graph (replayed per epoch on `stream`).
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  float2* graph_object = nullptr;
+  float2* graph_probe = nullptr;
+  int graph_verify = -1;
+  int64_t graph_counts[4] = {0, 0, 0, 0};
   float* d_wq = nullptr;          // [m][m]
   void* d_levels = nullptr;       // all multigrid arrays
   int32_t* d_orders = nullptr;    // [cap_orders]
@@ -177,6 +186,9 @@ void free_all(emg_ctx* c) {
   cudaFree(c->d_scalar);
   cudaFree(c->d_norm);
   cudaFree(c->d_mq);
+  cudaFree(c->d_epoch_order);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->d_wq);
   cudaFree(c->d_levels);
   cudaFree(c->d_orders);
@@ -282,10 +294,10 @@ void permutation(uint64_t seed, int64_t epoch, int32_t n, int32_t* out) {
 }
 
 // Seeds max|Q|^2 of the bound probe into slot 0 before a call's first minibatch.
-emg_status seed_probe_max(emg_ctx* c) {
-  EMG_CUDA(c, cudaMemsetAsync(c->d_mq, 0, 2 * sizeof(unsigned), c->stream));
+emg_status seed_probe_max(emg_ctx* c, cudaStream_t s) {
+  EMG_CUDA(c, cudaMemsetAsync(c->d_mq, 0, 2 * sizeof(unsigned), s));
   LaunchMark mk(c, kKindOther);
-  cudaError_t e = emg::launch_probe_max(c->probe, c->m, c->d_mq, c->stream);
+  cudaError_t e = emg::launch_probe_max(c->probe, c->m, c->d_mq, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "k_probe_max launch");
   return EMG_OK;
 }
@@ -293,7 +305,8 @@ emg_status seed_probe_max(emg_ctx* c) {
 // Enqueues one minibatch: probe prep, per-position step, combine.  `seq` is the
 // minibatch's index within the current call: it selects which max|Q|^2 slot
 // the prep reads and which one the combine fills.
-emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_phi_out, int seq) {
+emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_phi_out, int seq,
+                             cudaStream_t strm) {
   if (!c->object || !c->probe) return fail(c, EMG_EINVAL, "no state bound");
   PrepArgs pa = c->prep;
   pa.probe = c->probe;  // the probe bound right now (emg_reconstruct_host swaps it)
@@ -302,7 +315,7 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   cudaError_t e;
   {
     LaunchMark mk(c, kKindPrep);
-    e = emg::launch_prep(pa, c->stream);
+    e = emg::launch_prep(pa, strm);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_prep launch");
   StepArgs sa{};
@@ -327,7 +340,7 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   sa.phi_after = c->d_phi_after;
   {
     LaunchMark mk(c, kKindStep);
-    e = emg::launch_step(c->m, b, sa, c->stream);
+    e = emg::launch_step(c->m, b, sa, strm);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_step launch");
   ApplyArgs aa{};
@@ -349,7 +362,7 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   aa.tiles_y = (c->n_rows + emg::kApplyTile - 1) / emg::kApplyTile;
   {
     LaunchMark mk(c, kKindApply);
-    e = emg::launch_apply(aa, c->stream);
+    e = emg::launch_apply(aa, strm);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_apply launch");
   return EMG_OK;
@@ -357,6 +370,49 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
 
 emg_status check_bound(emg_ctx* c) {
   if (!c->object || !c->probe) return fail(c, EMG_EINVAL, "no state bound (call emg_bind_state)");
+  return EMG_OK;
+}
+
+// Captures one epoch (probe-max seed + all minibatches reading d_epoch_order)
+// as a graph for the currently bound state; reused until the state changes.
+emg_status ensure_epoch_graph(emg_ctx* c) {
+  if (c->graph && c->graph_object == c->object && c->graph_probe == c->probe &&
+      c->graph_verify == c->verify)
+    return EMG_OK;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  int64_t before[kKinds];
+  for (int i = 0; i < kKinds; ++i) before[i] = c->launches[i];
+  EMG_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  emg_status st = seed_probe_max(c, c->cap_stream);
+  const int N = c->n_pos, B = c->par.minibatch;
+  int seq = 0;
+  for (int b0 = 0; st == EMG_OK && b0 < N; b0 += B) {
+    const int b = (N - b0 < B) ? N - b0 : B;
+    st = enqueue_minibatch(c, c->d_epoch_order + b0, b, c->d_phi + b0, seq++, c->cap_stream);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
+  for (int i = 0; i < kKinds; ++i) {
+    c->graph_counts[i] = c->launches[i] - before[i];
+    c->launches[i] = before[i];
+  }
+  if (st != EMG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaStreamEndCapture");
+  const cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    c->graph = nullptr;
+    return cuda_fail(c, ie, "cudaGraphInstantiate");
+  }
+  c->graph_object = c->object;
+  c->graph_probe = c->probe;
+  c->graph_verify = c->verify;
   return EMG_OK;
 }
 
@@ -384,13 +440,24 @@ emg_status run_epochs_impl(emg_ctx* c, int32_t n_epochs, const int32_t* order, d
   if (st != EMG_OK) return st;
   if ((st = ensure_hist(c, n_epochs)) != EMG_OK) return st;
   EMG_CUDA(c, cudaMemcpyAsync(c->d_orders, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
-  if ((st = seed_probe_max(c)) != EMG_OK) return st;
-  int seq = 0;
+  // Profiling times each launch with events, so it runs the epochs as direct
+  // launches; otherwise each epoch replays the captured graph.
+  const bool use_graph = !c->profile;
+  if (use_graph && (st = ensure_epoch_graph(c)) != EMG_OK) return st;
   for (int32_t e = 0; e < n_epochs; ++e) {
     const int32_t* ord = c->d_orders + (size_t)e * N;
-    for (int b0 = 0; b0 < N; b0 += B) {
-      const int b = (N - b0 < B) ? N - b0 : B;
-      if ((st = enqueue_minibatch(c, ord + b0, b, c->d_phi + b0, seq++)) != EMG_OK) return st;
+    if (use_graph) {
+      EMG_CUDA(c, cudaMemcpyAsync(c->d_epoch_order, ord, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                  c->stream));
+      EMG_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
+      for (int i = 0; i < kKinds; ++i) c->launches[i] += c->graph_counts[i];
+    } else {
+      if ((st = seed_probe_max(c, c->stream)) != EMG_OK) return st;
+      int seq = 0;
+      for (int b0 = 0; b0 < N; b0 += B) {
+        const int b = (N - b0 < B) ? N - b0 : B;
+        if ((st = enqueue_minibatch(c, ord + b0, b, c->d_phi + b0, seq++, c->stream)) != EMG_OK) return st;
+      }
     }
     if (running) {
       c->launches[kKindOther] += 1;
@@ -504,9 +571,11 @@ emg_status emg_create(emg_ctx** out, const emg_problem* pr, const emg_params* pa
       dmalloc(&c->d_mu, (size_t)B) || dmalloc(&c->d_phi, (size_t)N) ||
       dmalloc(&c->d_phi_after, (size_t)B) || dmalloc(&c->d_partial, (size_t)N) ||
       dmalloc(&c->d_scalar, (size_t)64) || dmalloc(&c->d_norm, (size_t)1024) || dmalloc(&c->d_mq, (size_t)2) ||
+      dmalloc(&c->d_epoch_order, (size_t)N) ||
       dmalloc(&c->d_wq, mm))
     return bail(EMG_ENOMEM);
   if (cudaMallocHost(&c->h_scalar, 64 * sizeof(double)) != cudaSuccess) return bail(EMG_ENOMEM);
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(EMG_ECUDA);
   if (alloc_levels(c) != EMG_OK) return bail(EMG_ENOMEM);
   c->h_pos.resize((size_t)2 * N);
   if (cudaMemcpyAsync(c->h_pos.data(), pr->pos, c->h_pos.size() * sizeof(int32_t), cudaMemcpyDefault,
@@ -562,8 +631,8 @@ emg_status emg_step_minibatch(emg_ctx* c, const int32_t* idx, int32_t b, double*
   DeviceGuard g(c->device);
   if ((st = ensure_orders(c, (size_t)c->n_pos)) != EMG_OK) return st;
   EMG_CUDA(c, cudaMemcpyAsync(c->d_orders, idx, (size_t)b * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
-  if ((st = seed_probe_max(c)) != EMG_OK) return st;
-  if ((st = enqueue_minibatch(c, c->d_orders, b, c->d_phi, 0)) != EMG_OK) return st;
+  if ((st = seed_probe_max(c, c->stream)) != EMG_OK) return st;
+  if ((st = enqueue_minibatch(c, c->d_orders, b, c->d_phi, 0, c->stream)) != EMG_OK) return st;
   c->last_b = b;
   if (sampled_misfit) {
     cudaError_t e = emg::launch_sum(c->d_phi, b, 1.0, c->d_scalar, c->stream);

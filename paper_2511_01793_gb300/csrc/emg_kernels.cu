@@ -965,19 +965,34 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
     float2 num = czero();
     float den = 0.f;
     bool covered = false;
-    for (int t = 0; t < cnt; ++t) {
-      const int lr = row - list[3 * t + 1], lc = col - list[3 * t + 2];
-      if ((unsigned)lr < (unsigned)m && (unsigned)lc < (unsigned)m) {
-        const int kb = list[3 * t];
-        const float2 v = a.zt[(size_t)kb * mm + lr * m + lc];
-        covered = true;
-        if (a.combine == 0) {
-          const float w = a.wq[lr * m + lc];
-          num = make_float2(fmaf(w, v.x, num.x), fmaf(w, v.y, num.y));
-          den += w;
-        } else {
-          num = cadd(num, v);
-          den += 1.f;
+    // patches in minibatch order; loads of four patches are issued together
+    for (int t0 = 0; t0 < cnt; t0 += 4) {
+      float2 v[4];
+      float w[4];
+      bool in[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int t = t0 + u;
+        in[u] = false;
+        if (t < cnt) {
+          const int lr = row - list[3 * t + 1], lc = col - list[3 * t + 2];
+          in[u] = (unsigned)lr < (unsigned)m && (unsigned)lc < (unsigned)m;
+          if (in[u]) {
+            v[u] = a.zt[(size_t)list[3 * t] * mm + lr * m + lc];
+            w[u] = a.combine == 0 ? a.wq[lr * m + lc] : 1.f;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (in[u]) {
+          covered = true;
+          if (a.combine == 0) {
+            num = make_float2(fmaf(w[u], v[u].x, num.x), fmaf(w[u], v[u].y, num.y));
+          } else {
+            num = cadd(num, v[u]);
+          }
+          den += w[u];
         }
       }
     }
@@ -995,10 +1010,21 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
     float2 s = czero();
     int cnt = 0;
     if (p < (int)mm) {
-      for (int kb = g; kb < a.b; kb += kApplyProbeGroups) {
-        if (a.mu[kb] > 0.f) {
-          s = cadd(s, a.qt[(size_t)kb * mm + p]);
-          ++cnt;
+      for (int kb0 = g; kb0 < a.b; kb0 += 4 * kApplyProbeGroups) {
+        float2 v[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int kb = kb0 + u * kApplyProbeGroups;
+          ok[u] = kb < a.b && a.mu[kb] > 0.f;
+          if (ok[u]) v[u] = a.qt[(size_t)kb * mm + p];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (ok[u]) {
+            s = cadd(s, v[u]);
+            ++cnt;
+          }
         }
       }
     }

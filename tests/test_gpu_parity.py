@@ -317,3 +317,20 @@ def test_host_buffer_entry_point_equals_device_path(lib, torch):
     assert np.array_equal(z1, zh.astype(np.complex128)) and np.array_equal(q1, qh.astype(np.complex128))
     c1.close()
     c2.close()
+
+
+def test_graph_replay_equals_direct_launches(lib, torch):
+    """Epochs replayed from the captured CUDA graph equal direct launches bitwise
+    (profiling mode runs the direct path)."""
+    case = Case(n=2 * 64 + 40, m=64, side=4, noise_peak=1e5)
+    p = oracle_params(minibatch=5, levels=3, prolong="bilinear")
+    c1 = make_context(lib, case, p, seed=3)
+    lib.emg_run_epochs(c1.ctx, 3)
+    c2 = make_context(lib, case, p, seed=3)
+    lib.emg_set_profiling(c2.ctx, True)
+    lib.emg_run_epochs(c2.ctx, 3)
+    a1, b1 = state(c1)
+    a2, b2 = state(c2)
+    assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
+    c1.close()
+    c2.close()
