@@ -28,6 +28,15 @@ template <> struct StepThreads<128> { static constexpr int value = 512; };
 
 __device__ __forceinline__ float2 czero() { return make_float2(0.f, 0.f); }
 
+// Programmatic dependent launch: the minibatch kernels (prep -> step ->
+// combine) are launched so that each may start while its predecessor drains.
+// pdl_wait() blocks until the predecessor grid has finished and its writes are
+// visible; everything before it may only read data that no predecessor
+// writes (scan order, positions, amplitudes).  pdl_trigger() lets the
+// successor launch.  Both are no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ float2 gather_obj(const float2* __restrict__ z, int n_rows, int n_cols,
                                              int gr, int gc) {
   if ((unsigned)gr < (unsigned)n_rows && (unsigned)gc < (unsigned)n_cols)
@@ -57,23 +66,21 @@ __device__ __forceinline__ float2 geometric_mean_aligned(float2 x, float2 xp) {
   return y;
 }
 
-// Principal square root by Kahan's formula with hardware reciprocal square
-// roots (rsqrtf) for |w| and the half-sum: s = (|x| + |w|)/2, t = sqrt(s),
-// root = (t, y/(2t)) for x >= 0 and (|y|/(2t), sign(y) t) otherwise.
-__device__ __forceinline__ float2 csqrt_principal_fast(float2 w) {
+// y with y^2 = x * xp and Re(y conj(x)) >= 0 (Eq. geomean), branch-free.
+// With w = x xp = u + i v, s = (|u| + |w|)/2, t = sqrt(s), h = 1/(2t):
+// (t, v h) squares to w when u >= 0 (Kahan's half-angle form), and (v h, t)
+// squares to w when u < 0 (its real part is (v^2 - 4 s^2)/(4 s) = u); either
+// root is then negated if it points away from x.  Square roots come from rsqrtf.
+__device__ __forceinline__ float2 geometric_mean_aligned_fast(float2 x, float2 xp) {
+  const float2 w = cmul(x, xp);
   const float n = fmaf(w.x, w.x, w.y * w.y);
-  if (n == 0.f) return czero();
   const float mag = n * rsqrtf(n);
   const float s = 0.5f * (fabsf(w.x) + mag);
   const float rt = rsqrtf(s);
-  const float t = s * rt, h = 0.5f * rt;
-  if (w.x >= 0.f) return make_float2(t, w.y * h);
-  return make_float2(fabsf(w.y) * h, copysignf(t, w.y));
-}
-
-__device__ __forceinline__ float2 geometric_mean_aligned_fast(float2 x, float2 xp) {
-  float2 y = csqrt_principal_fast(cmul(x, xp));
-  if (fmaf(y.x, x.x, y.y * x.y) < 0.f) y = make_float2(-y.x, -y.y);
+  const float t = s * rt, vh = w.y * (0.5f * rt);
+  float2 y = w.x >= 0.f ? make_float2(t, vh) : make_float2(vh, t);
+  const float sgn = fmaf(y.x, x.x, y.y * x.y) < 0.f ? -1.f : 1.f;
+  y = n > 0.f ? make_float2(sgn * y.x, sgn * y.y) : czero();
   return y;
 }
 
@@ -279,6 +286,8 @@ __global__ void __launch_bounds__(kPrepTileThreads) k_prep_tile(const PrepArgs a
   const int m = a.m, L = a.levels, tile = a.tile, halo = a.halo;
   const int tiles_per_row = m / tile;
   const int R0 = (blockIdx.x / tiles_per_row) * tile, C0 = (blockIdx.x % tiles_per_row) * tile;
+  pdl_trigger();
+  pdl_wait();  // the probe and max|Q|^2 come from the previous combine
   const float MQ = __uint_as_float(*a.mq_read);
   if (blockIdx.x == 0 && tid == 0) *a.mq_next = 0u;
 
@@ -626,7 +635,7 @@ __device__ __forceinline__ T prolong_halo(const T* y, int sl, int wc, int lr, in
 }
 
 template <int M>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::value)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::value, 1)
     k_step2(const StepArgs a) {
   constexpr int NT = Step2Threads<M>::value;
   constexpr int H = M / 2, SR = M + 1, SC = H + 1;
@@ -662,6 +671,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
 #pragma unroll
     for (int i = 0; i < N1; ++i) am_reg[t][i] = __ldg(amp + (i + N1 * k2) * M + lc);
   }
+  pdl_trigger();
+  pdl_wait();  // object, probe, max|Q|^2 and level arrays come from earlier kernels
   const float MQ = __uint_as_float(*a.mq);
   cl.barrier_arrive();  // completed (wait) before the first distributed shared memory access
 
@@ -775,9 +786,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
   if (a.levels > 1) {
     {  // restrict level 0 -> 1: z_1 = I_h^H (W_z z_k), R_1 = I_h^H (W_R R)
       constexpr int wc = M / 2, hc = wc / 2, sc = wc + 1;
+      constexpr int PC = hc * wc / NT;
+      static_assert(hc * wc % NT == 0, "coarse slab must split evenly");
       const float* Wz = a.lv.Wz[0];
       const float2* WR = a.lv.WR[0];
-      for (int p = tid; p < hc * wc; p += NT) {
+#pragma unroll
+      for (int t = 0; t < PC; ++t) {
+        const int p = tid + t * NT;
         const int i = p / wc, j = p % wc;
         float2 zs = czero(), rs = czero();
 #pragma unroll
@@ -835,6 +850,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
       const int wl = M >> l, hl = wl >> 1, sl = wl + 1, wc = wl >> 1, sc = wc + 1;
       const float2* G = a.lv.G[l];
       const float2* Q = a.lv.Q[l];
+#pragma unroll 4
       for (int p = tid; p < hl * wl; p += NT) {
         const int i = p / wl, j = p % wl, gi = rank * hl + i;
         const float2 pro = prolong_halo<float2>(Zl[l + 1], sc, wc, i, j, a.prolong);
@@ -923,6 +939,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
   const int n_tiles = a.tiles_x * a.tiles_y;
   const int m = a.m;
   const size_t mm = (size_t)m * m;
+  pdl_trigger();
   if ((int)blockIdx.x < n_tiles) {
     const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x % a.tiles_x;
     const int r0 = ty * kApplyTile, c0 = tx * kApplyTile;
@@ -962,6 +979,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
     const int cnt = total;
     const int row = r0 + tid / kApplyTile, col = c0 + tid % kApplyTile;
     if (cnt == 0 || row >= a.n_rows || col >= a.n_cols) return;
+    pdl_wait();  // patches z~_k and weights come from the step and prep kernels
     float2 num = czero();
     float den = 0.f;
     bool covered = false;
@@ -1005,6 +1023,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
       a.object[gi] = cadd(z, csub(num, cscale(z, den)));
     }
   } else {
+    pdl_wait();  // probes Q~_k come from the step kernel
     const int lane = tid & 31, g = tid >> 5;
     const int p = (blockIdx.x - n_tiles) * 32 + lane;
     float2 s = czero();
@@ -1257,6 +1276,22 @@ cudaError_t set_aux_smem() {
 }  // namespace
 
 // Dynamic shared memory per CTA; 227 KB minus room for the kernels' static reductions.
+// Launch with programmatic stream serialisation (see pdl_wait / pdl_trigger).
+template <typename Kernel, typename... Args>
+cudaError_t launch_pdl(Kernel kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 int step_smem_limit() { return 227 * 1024 - 1024; }
 
 size_t step_smem_bytes(int m, int levels) {
@@ -1328,7 +1363,8 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
   PrepArgs t = a;
   if (a.mq_read && prep_tiled_config(t)) {
     const int tiles = (t.m / t.tile) * (t.m / t.tile);
-    k_prep_tile<<<tiles, kPrepTileThreads, prep_tile_smem(t), s>>>(t);
+    cudaError_t e = launch_pdl(k_prep_tile, dim3(tiles), dim3(kPrepTileThreads), prep_tile_smem(t), s, t);
+    if (e != cudaSuccess) return e;
   } else {
     k_prep<<<1, kPrepThreads, 0, s>>>(a);
   }
@@ -1345,7 +1381,9 @@ cudaError_t launch_probe_max(const float2* probe, int m, unsigned* slot, cudaStr
 
 template <int M>
 cudaError_t launch_step2_t(int b, const StepArgs& a, cudaStream_t s) {
-  k_step2<M><<<2 * b, Step2Threads<M>::value, step2_smem_elems<M>() * sizeof(float2), s>>>(a);
+  cudaError_t e = launch_pdl(k_step2<M>, dim3(2 * b), dim3(Step2Threads<M>::value),
+                             step2_smem_elems<M>() * sizeof(float2), s, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -1359,7 +1397,8 @@ cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
   const int n_tiles = a.tiles_x * a.tiles_y;
   const int n_probe = (a.m * a.m + 31) / 32;
   const size_t bytes = (size_t)a.b * 3 * sizeof(int);
-  k_apply<<<n_tiles + n_probe, kApplyThreads, bytes, s>>>(a);
+  cudaError_t e = launch_pdl(k_apply, dim3(n_tiles + n_probe), dim3(kApplyThreads), bytes, s, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
