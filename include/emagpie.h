@@ -66,7 +66,7 @@ typedef struct emg_ctx emg_ctx; /* opaque, library-owned */
  *  intensity  device float32 [n_pos][m][m]: d_k with DC at [0][0].  Negative
  *             values are clamped to 0 before the square root.  Read only
  *             during emg_create (the library keeps sqrt(d) in its own layout).
- *  m          16, 32, 64 or 128.
+ *  m          16, 32, 64, 128 or 256.
  */
 typedef struct emg_problem {
   int32_t n_rows, n_cols;
@@ -178,6 +178,23 @@ emg_status emg_set_verify(emg_ctx* ctx, int32_t verify);
 emg_status emg_run_epochs(emg_ctx* ctx, int32_t n_epochs, const int32_t* order,
                           double* running_misfit, double* misfit);
 
+/*
+ * Exit-wave misfit and its Wirtinger gradients (Sec. 2.1) at an arbitrary
+ * (object, probe), which need not be the bound state:
+ *   Phi = 1/2 sum_k ||Q . P_k z - R_k(Q, P_k z)||^2,
+ *   grad_z Phi = sum_k P_k^T [conj(Q) (Q . P_k z - R_k)],
+ *   grad_Q Phi = sum_k conj(P_k z) (Q . P_k z - R_k),
+ * in the convention d/dRe + i d/dIm (twice the conjugate Wirtinger derivative,
+ * the convention PyTorch uses for complex autograd).  R_k is recomputed (no
+ * exit waves are stored); positions are processed in chunks of
+ * params.minibatch and summed in a fixed order (deterministic).
+ *  object, probe            device complex64 [n_rows][n_cols], [m][m] (read only)
+ *  grad_object, grad_probe  device complex64, same shapes, overwritten; either may be NULL
+ *  misfit                   host double or NULL (synchronises when not NULL)
+ */
+emg_status emg_misfit_gradient(emg_ctx* ctx, const float* object, const float* probe,
+                               float* grad_object, float* grad_probe, double* misfit);
+
 /* Phi(Q, z) = 1/2 sum_k ||Q . P_k z - R_k||^2 of the bound state (host *out; synchronises). */
 emg_status emg_misfit(emg_ctx* ctx, double* out);
 
@@ -245,6 +262,7 @@ emg_status emg_profile_read(emg_ctx* ctx, double* ms, int64_t* launches);
  *  pos         device int32 [n_pos][2] patch corners, |row|, |col| < 2^24
  *  intensity   device float32 [n_pos][m][m] data d_k in natural order (DC at [0][0])
  *  idx, b      host int32 [b] positions of this minibatch, 1 <= b <= n_pos
+ *  m           16, 32, 64 or 128 (EMG_ENOTSUP for 256)
  *  params      as for emg_create (minibatch and seed are ignored)
  *
  * The result equals emg_step_minibatch on the same inputs.  Its only scratch

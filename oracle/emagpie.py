@@ -50,7 +50,7 @@ __all__ = [
     "joint_step", "minibatch_step", "run_epochs", "sequential_sweep",
     "forward_intensity", "dp_avg", "dp_avg_scale", "splitmix64_stream",
     "schedule_permutation", "magnitude_error", "illuminated_region",
-    "aligned_errors",
+    "aligned_errors", "misfit_gradients",
 ]
 
 
@@ -155,6 +155,26 @@ def wirtinger_gradients(Q, z_k, a_k):
     R = revised_exit_wave(Q, z_k, a_k)
     e = Q * z_k - R
     return np.conj(Q) * e, np.conj(z_k) * e
+
+
+def misfit_gradients(Q, z, pos, a):
+    """Phi(Q, z) and its gradients over all positions (Sec. 2.1, Eq. exit_misfit).
+
+    grad_z Phi = sum_k P_k^T [conj(Q) (Q z_k - R_k)] (patch pixels outside the
+    object drop out), grad_Q Phi = sum_k conj(z_k) (Q z_k - R_k).
+    """
+    m = Q.shape[0]
+    gz = np.zeros_like(z)
+    gq = np.zeros_like(Q)
+    phi = 0.0
+    for k in range(len(pos)):
+        z_k = select_patch(z, pos[k], m)
+        phi += exit_wave_misfit_k(Q, z_k, a[k])
+        g_zk, g_q = wirtinger_gradients(Q, z_k, a[k])
+        obj, pat = _patch_slices(z.shape, pos[k], m)
+        gz[obj] += g_zk[pat]
+        gq += g_q
+    return phi, gz, gq
 
 
 def forward_intensity(Q, z, pos) -> np.ndarray:

@@ -26,7 +26,8 @@ __all__ = [
     "emg_create", "emg_set_intensity", "emg_bind_state", "emg_normalize_probe",
     "emg_step_minibatch", "emg_position_stats", "emg_set_verify", "emg_run_epochs", "emg_misfit",
     "emg_set_epoch", "emg_schedule_permutation", "emg_reconstruct_host",
-    "emg_simulate_intensity", "emg_fft2", "emg_step_minibatch_noalloc", "emg_set_profiling",
+    "emg_simulate_intensity", "emg_fft2", "emg_step_minibatch_noalloc", "emg_misfit_gradient",
+    "emg_set_profiling",
     "emg_profile_read",
     "emg_last_error", "emg_destroy", "Context",
 ]
@@ -84,6 +85,7 @@ _SIGS = {
     "emg_step_minibatch_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_int32,
                                                   _VP, _VP, ctypes.c_int32, _I32P, ctypes.c_int32,
                                                   ctypes.POINTER(EmgParams), _VP]),
+    "emg_misfit_gradient": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _F64P]),
     "emg_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "emg_profile_read": (ctypes.c_int, [_VP, _F64P, ctypes.POINTER(ctypes.c_int64)]),
     "emg_last_error": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_char_p)]),
@@ -265,6 +267,17 @@ def emg_step_minibatch_noalloc(object_ptr: int, n_rows: int, n_cols: int, probe_
                                              intensity_ptr, n_pos, _ptr_i32(a), len(a),
                                              ctypes.byref(params), _VP(stream)),
            "emg_step_minibatch_noalloc")
+
+
+def emg_misfit_gradient(ctx: int, object_ptr: int, probe_ptr: int, grad_object_ptr: int = 0,
+                        grad_probe_ptr: int = 0, want_misfit: bool = True) -> Optional[float]:
+    """Misfit and Wirtinger gradients at (object, probe); gradient pointers may be 0."""
+    out = ctypes.c_double()
+    _check(load().emg_misfit_gradient(ctx, object_ptr, probe_ptr, grad_object_ptr or None,
+                                      grad_probe_ptr or None,
+                                      ctypes.byref(out) if want_misfit else None),
+           "emg_misfit_gradient", ctx)
+    return out.value if want_misfit else None
 
 
 def emg_set_profiling(ctx: int, enable: bool) -> None:

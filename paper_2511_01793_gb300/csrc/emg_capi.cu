@@ -145,7 +145,7 @@ cudaError_t ensure_device_init(int dev) {
   return e;
 }
 
-bool valid_m(int m) { return m == 16 || m == 32 || m == 64 || m == 128; }
+bool valid_m(int m) { return m == 16 || m == 32 || m == 64 || m == 128 || m == 256; }
 
 emg_status validate_params(emg_ctx* c, const emg_params* p, int m, int n_pos) {
   if (!p) return fail(c, EMG_EINVAL, "params is NULL");
@@ -162,8 +162,8 @@ emg_status validate_params(emg_ctx* c, const emg_params* p, int m, int n_pos) {
   if (p->scatter != EMG_SCATTER_DETERMINISTIC) return fail(c, EMG_EINVAL, "unknown scatter mode");
   if (p->joint != 0 && p->joint != 1) return fail(c, EMG_EINVAL, "joint must be 0 or 1");
   if (!(p->w_eps >= 0.f) || !isfinite(p->w_eps)) return fail(c, EMG_EINVAL, "w_eps must be finite and >= 0");
-  if (emg::step_smem_bytes(m, p->levels) > (size_t)emg::step_smem_limit())
-    return fail(c, EMG_ENOTSUP, "too many levels for the shared-memory budget of this m");
+  if (!emg::step_supported(m, p->levels))
+    return fail(c, EMG_ENOTSUP, "too many multigrid levels for this probe size");
   return EMG_OK;
 }
 
@@ -758,6 +758,58 @@ emg_status emg_fft2(const float* in, float* out, int32_t m, int32_t count, int32
   if (cudaGetDevice(&dev) != cudaSuccess || ensure_device_init(dev) != cudaSuccess) return EMG_ECUDA;
   cudaError_t e = emg::launch_fft2(m, (const float2*)in, (float2*)out, count, inverse, (cudaStream_t)stream);
   return e == cudaSuccess ? EMG_OK : EMG_ECUDA;
+}
+
+emg_status emg_misfit_gradient(emg_ctx* c, const float* object, const float* probe, float* grad_object,
+                               float* grad_probe, double* misfit) {
+  if (!c) return EMG_EINVAL;
+  if (!object || !probe) return fail(c, EMG_EINVAL, "object or probe is NULL");
+  DeviceGuard g(c->device);
+  const int N = c->n_pos, B = c->par.minibatch;
+  for (int first = 0; first < N; first += B) {
+    const int b = (N - first < B) ? N - first : B;
+    emg::GradArgs ga{};
+    ga.object = (const float2*)object;
+    ga.probe = (const float2*)probe;
+    ga.pos = c->d_pos;
+    ga.amp = c->d_amp;
+    ga.first = first;
+    ga.n_rows = c->n_rows;
+    ga.n_cols = c->n_cols;
+    ga.gz = c->d_zt;
+    ga.gq = c->d_qt;
+    ga.phi = c->d_phi + first;
+    cudaError_t e = emg::launch_gradient(c->m, b, ga, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "k_gradc launch");
+    c->launches[kKindOther] += 1;
+    if (grad_object || grad_probe) {
+      emg::GradReduceArgs ra{};
+      ra.pos = c->d_pos;
+      ra.first = first;
+      ra.b = b;
+      ra.n_rows = c->n_rows;
+      ra.n_cols = c->n_cols;
+      ra.m = c->m;
+      ra.accumulate = first > 0;
+      ra.gz = c->d_zt;
+      ra.gq = c->d_qt;
+      ra.grad_object = (float2*)grad_object;
+      ra.grad_probe = (float2*)grad_probe;
+      ra.tiles_x = (c->n_cols + emg::kApplyTile - 1) / emg::kApplyTile;
+      ra.tiles_y = (c->n_rows + emg::kApplyTile - 1) / emg::kApplyTile;
+      e = emg::launch_grad_reduce(ra, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "k_grad_reduce launch");
+      c->launches[kKindOther] += 1;
+    }
+  }
+  if (misfit) {
+    cudaError_t e = emg::launch_sum(c->d_phi, N, 1.0, c->d_scalar, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "k_sum launch");
+    EMG_CUDA(c, cudaMemcpyAsync(c->h_scalar, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+    *misfit = c->h_scalar[0];
+  }
+  return EMG_OK;
 }
 
 emg_status emg_set_profiling(emg_ctx* c, int32_t enable) {

@@ -90,6 +90,7 @@ template <> struct FftPlan<16> { static constexpr int N1 = 4, N2 = 4; };
 template <> struct FftPlan<32> { static constexpr int N1 = 4, N2 = 8; };
 template <> struct FftPlan<64> { static constexpr int N1 = 8, N2 = 8; };
 template <> struct FftPlan<128> { static constexpr int N1 = 8, N2 = 16; };
+template <> struct FftPlan<256> { static constexpr int N1 = 16, N2 = 16; };
 
 // Storage slot -> frequency of the 1-D transform.
 template <int M>

@@ -72,6 +72,48 @@ struct ApplyArgs {
   int tiles_x, tiles_y;         // object tiles of kApplyTile x kApplyTile pixels
 };
 
+// Forward-only cluster kernels (m up to 256): misfit partials, simulated
+// intensities, forward / inverse 2-D DFT of natural-order tiles.
+struct FwdArgs {
+  const float2* object;
+  const float2* probe;
+  const int32_t* pos;
+  const float* amp;             // storage order (misfit)
+  int n_rows, n_cols;
+  double* partial;              // [count] misfit per position (mode 0)
+  float* out_intensity;         // [count][m][m] natural order (mode 1)
+  const float2* in;             // [count][m][m] natural order (modes 2, 3)
+  float2* out;                  // [count][m][m] natural order (modes 2, 3)
+};
+
+// Wirtinger gradients of the exit-wave misfit per position (Sec. 2.1):
+// gz_k = conj(Q) (psi_k - R_k), gq_k = conj(z_k) (psi_k - R_k).
+struct GradArgs {
+  const float2* object;
+  const float2* probe;
+  const int32_t* pos;
+  const float* amp;
+  int first, n_rows, n_cols;    // positions first .. first + b - 1
+  float2* gz;                   // [b][m][m]
+  float2* gq;                   // [b][m][m]
+  double* phi;                  // [b]
+};
+
+// Sums the patch gradients of one chunk into the object / probe gradients.
+struct GradReduceArgs {
+  const int32_t* pos;
+  int first, b, n_rows, n_cols, m, accumulate;
+  const float2* gz;
+  const float2* gq;
+  float2* grad_object;          // [n_rows][n_cols] or null
+  float2* grad_probe;           // [m][m] or null
+  int tiles_x, tiles_y;
+};
+
+cudaError_t launch_gradient(int m, int b, const GradArgs& a, cudaStream_t s);
+cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t s);
+bool step_supported(int m, int levels);
+
 constexpr int kApplyTile = 16;
 constexpr int kApplyThreads = 256;      // one object pixel per thread
 constexpr int kApplyProbeGroups = 8;    // probe blocks: 32 pixels x 8 position groups

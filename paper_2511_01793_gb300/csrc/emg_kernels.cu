@@ -600,26 +600,66 @@ __global__ void __launch_bounds__(StepThreads<M>::value) k_step(const StepArgs a
 }
 
 // ---------------------------------------------------------------------------
-// One scan position per cluster of two CTAs (m = 64, 128).
+// One scan position per cluster of C CTAs (m = 64, 128: C = 2; m = 256: C = 8).
 //
-// CTA `rank` owns patch rows [rank m/2, (rank+1) m/2) for the gather, the row
+// CTA `rank` owns patch rows [rank m/C, (rank+1) m/C) for the gather, the row
 // FFT passes, the multigrid passes and the update, and storage columns
-// [rank m/2, (rank+1) m/2) for the column FFT passes and the modulus
+// [rank m/C, (rank+1) m/C) for the column FFT passes and the modulus
 // replacement.  The two transposes between row and column slabs go through
-// distributed shared memory; the multigrid up-pass reads the one coarse row
-// it needs from the peer (bilinear prolongation).  Per CTA the shared memory
-// is one row slab and one column slab (half of the single-CTA footprint), so
-// a minibatch of B positions occupies 2B SMs.
+// distributed shared memory; the multigrid up-pass reads the coarse rows
+// adjacent to its slab from the neighbouring ranks (bilinear prolongation).
+// Per CTA the shared memory is one row slab, one column slab and the object
+// slab, so a minibatch of B positions occupies C B SMs.
 namespace cg = cooperative_groups;
 
-template <int M> struct Step2Threads;
-template <> struct Step2Threads<64> { static constexpr int value = 256; };
-template <> struct Step2Threads<128> { static constexpr int value = 512; };
+template <int M> struct ClusterSize;
+template <> struct ClusterSize<16> { static constexpr int value = 2; };
+template <> struct ClusterSize<32> { static constexpr int value = 2; };
+template <> struct ClusterSize<64> { static constexpr int value = 2; };
+template <> struct ClusterSize<128> { static constexpr int value = 2; };
+template <> struct ClusterSize<256> { static constexpr int value = 8; };
 
-// Shared memory of k_step2 in float2: row slab, column slab, object slab z_k.
-template <int M>
-__host__ __device__ constexpr size_t step2_smem_elems() {
-  return (size_t)(M / 2) * (M + 1) + (size_t)M * (M / 2 + 1) + (size_t)(M / 2) * M;
+template <int M, int C>
+struct CTile {
+  static constexpr int H = M / C;              // rows of a row slab, columns of a column slab
+  static constexpr int SR = M + 1, SC = H + 1;  // odd strides: conflict-free lines
+  static constexpr int N1 = FftPlan<M>::N1, N2 = FftPlan<M>::N2;
+  static constexpr int NT = H * N1;            // one pass-A slot per thread
+  static constexpr int PER = H * M / NT;       // slab pixels per thread
+  static constexpr int SLOTS = H * N2 / NT;    // column pass-B slots per thread
+  static constexpr size_t smem_elems = (size_t)H * SR + (size_t)M * SC + (size_t)H * M;
+  static_assert(H * M % NT == 0 && H * N2 % NT == 0 && NT <= 1024, "slab must split evenly");
+};
+
+// Row slab (after the row passes) -> column slabs of all C CTAs.
+template <int M, int C>
+__device__ __forceinline__ void cluster_rows_to_cols(cg::cluster_group& cl, int rank, const float2* rowbuf,
+                                                     float2* colbuf, int tid) {
+  using T = CTile<M, C>;
+  for (int s = tid; s < T::H * M; s += T::NT) {
+    const int lr = s / M, e = s % M, d = e / T::H;
+    float2* dst = d == rank ? colbuf : cl.map_shared_rank(colbuf, d);
+    dst[(rank * T::H + lr) * T::SC + (e % T::H)] = rowbuf[lr * T::SR + e];
+  }
+}
+
+// Column slab -> row slabs of all C CTAs.
+template <int M, int C>
+__device__ __forceinline__ void cluster_cols_to_rows(cg::cluster_group& cl, int rank, const float2* colbuf,
+                                                     float2* rowbuf, int tid) {
+  using T = CTile<M, C>;
+  for (int s = tid; s < M * T::H; s += T::NT) {
+    const int r = s / T::H, lc = s % T::H, d = r / T::H;
+    float2* dst = d == rank ? rowbuf : cl.map_shared_rank(rowbuf, d);
+    dst[(r % T::H) * T::SR + rank * T::H + lc] = colbuf[r * T::SC + lc];
+  }
+}
+
+// Writes v into slot [rank] of `arr` in every CTA of the cluster.
+template <int C, typename V>
+__device__ __forceinline__ void cluster_publish(cg::cluster_group& cl, int rank, V* arr, V v) {
+#pragma unroll
+  for (int d = 0; d < C; ++d) *(d == rank ? &arr[rank] : cl.map_shared_rank(&arr[rank], d)) = v;
 }
 
 // (I_H^h y)(lr, c) for a coarse row slab stored with one halo row above and
@@ -634,33 +674,26 @@ __device__ __forceinline__ T prolong_halo(const T* y, int sl, int wc, int lr, in
   return lerp4<T>(v, y[i2 * sl + j], y[i * sl + j2], y[i2 * sl + j2]);
 }
 
-template <int M>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::value, 1)
-    k_step2(const StepArgs a) {
-  constexpr int NT = Step2Threads<M>::value;
-  constexpr int H = M / 2, SR = M + 1, SC = H + 1;
-  constexpr int N1 = FftPlan<M>::N1, N2 = FftPlan<M>::N2;
+template <int M, int C>
+__global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) {
+  using TL = CTile<M, C>;
+  constexpr int NT = TL::NT, H = TL::H, SR = TL::SR, SC = TL::SC;
+  constexpr int N1 = TL::N1, N2 = TL::N2, PER = TL::PER, SLOTS = TL::SLOTS;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const int peer = rank ^ 1;
-  constexpr int PER = H * M / NT;          // pixels of my row slab per thread
-  constexpr int SLOTS = H * N2 / NT;       // spectral slots per thread in the column pass B
-  static_assert(H * M % NT == 0 && H * N2 % NT == 0, "thread count must divide the slab");
   extern __shared__ float2 sm[];
   float2* rowbuf = sm;                     // H x SR: my patch rows
   float2* colbuf = sm + H * SR;            // M x SC: my storage columns (all rows); multigrid buffers later
   float2* zbuf = colbuf + M * SC;          // H x M: z_k on my rows (gathered once)
-  __shared__ float xf[2];
-  __shared__ double xd[2], xd2[2];
+  __shared__ float xf[C];
+  __shared__ double xd[C], xd2[C];
   __shared__ double redd[2];
   __shared__ float redf[NT / 32];
   const int tid = threadIdx.x;
-  const int kb = blockIdx.x >> 1;
+  const int kb = blockIdx.x / C;
   const int k = a.order[kb];
   const int o_r = a.pos[2 * k], o_c = a.pos[2 * k + 1];
   const int row0 = rank * H;
-  float2* peer_col = cl.map_shared_rank(colbuf, peer);
-  float2* peer_row = cl.map_shared_rank(rowbuf, peer);
 
   // amplitudes of my spectral slots: issued now, consumed after the row passes
   const float* amp = a.amp + (size_t)k * M * M + rank * H;
@@ -693,19 +726,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
   __syncthreads();
   gpass_b<M, H, SR, 1, NT, false>(rowbuf, tid);
   __syncthreads();
-  cl.barrier_wait();  // both CTAs resident
+  cl.barrier_wait();  // all CTAs of the cluster resident
   // transpose 1: my rows x all storage columns -> column slabs
-  for (int s = tid; s < H * M; s += NT) {
-    const int lr = s / M, e = s % M;
-    float2* dst = (e / H) == rank ? colbuf : peer_col;
-    dst[(row0 + lr) * SC + (e % H)] = rowbuf[lr * SR + e];
-  }
-  if (tid == 0) {
-    xf[rank] = mu_part;
-    *cl.map_shared_rank(&xf[rank], peer) = mu_part;
-  }
+  cluster_rows_to_cols<M, C>(cl, rank, rowbuf, colbuf, tid);
+  if (tid == 0) cluster_publish<C>(cl, rank, xf, mu_part);
   cl.sync();
-  const float mu = fmaxf(xf[0], xf[1]);
+  float mu = xf[0];
+#pragma unroll
+  for (int d = 1; d < C; ++d) mu = fmaxf(mu, xf[d]);
 
   // a2 (columns) + a3 + a4 (columns) on my storage columns
   gpass_a_fwd<M, H, 1, SC, NT>(colbuf, tid);
@@ -741,15 +769,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
   gpass_a_inv<M, H, 1, SC, NT>(colbuf, tid);
   const double phi_part = block_sum_f<NT>(acc, redf, redd);  // includes the barrier after the pass
   // transpose 2: all rows x my columns -> row slabs
-  for (int s = tid; s < M * H; s += NT) {
-    const int r = s / H, lc = s % H;
-    float2* dst = (r / H) == rank ? rowbuf : peer_row;
-    dst[(r % H) * SR + rank * H + lc] = colbuf[r * SC + lc];
-  }
-  if (tid == 0) {
-    xd[rank] = phi_part;
-    *cl.map_shared_rank(&xd[rank], peer) = phi_part;
-  }
+  cluster_cols_to_rows<M, C>(cl, rank, colbuf, rowbuf, tid);
+  if (tid == 0) cluster_publish<C>(cl, rank, xd, phi_part);
   cl.sync();
   // a4: inverse row passes -> R (natural order) on my rows
   gpass_b<M, H, SR, 1, NT, true>(rowbuf, tid);
@@ -764,7 +785,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
   {
     size_t off = 0;
     for (int l = 1; l < a.levels; ++l) {
-      const int wl = M >> l, hl = wl >> 1, sl = wl + 1;
+      const int wl = M >> l, hl = wl / C, sl = wl + 1;
       Zl[l] = colbuf + off + sl;
       off += (size_t)(hl + 2) * sl;
       Rl[l] = colbuf + off;
@@ -772,20 +793,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
     }
   }
   // Copies the rows of the coarse correction at level l adjacent to my slab
-  // (from the peer, or my own edge row where the patch ends) into the halo.
+  // (from the neighbouring ranks, or my own edge row where the patch ends).
   auto fill_halo = [&](int l) {
-    const int wl = M >> l, hl = wl >> 1, sl = wl + 1;
+    const int wl = M >> l, hl = wl / C, sl = wl + 1;
     float2* Z = Zl[l];
-    const float2* Zp = cl.map_shared_rank(Zl[l], peer);
+    const float2* Zup = rank > 0 ? cl.map_shared_rank(Zl[l], rank - 1) : Z;
+    const float2* Zdn = rank < C - 1 ? cl.map_shared_rank(Zl[l], rank + 1) : Z;
     for (int j = tid; j < wl; j += NT) {
-      Z[-sl + j] = rank == 0 ? Z[j] : Zp[(hl - 1) * sl + j];
-      Z[hl * sl + j] = rank == 0 ? Zp[j] : Z[(hl - 1) * sl + j];
+      Z[-sl + j] = rank > 0 ? Zup[(hl - 1) * sl + j] : Z[j];
+      Z[hl * sl + j] = rank < C - 1 ? Zdn[j] : Z[(hl - 1) * sl + j];
     }
   };
   const bool halo = a.prolong != 0;
   if (a.levels > 1) {
     {  // restrict level 0 -> 1: z_1 = I_h^H (W_z z_k), R_1 = I_h^H (W_R R)
-      constexpr int wc = M / 2, hc = wc / 2, sc = wc + 1;
+      constexpr int wc = M / 2, hc = wc / C, sc = wc + 1;
       constexpr int PC = hc * wc / NT;
       static_assert(hc * wc % NT == 0, "coarse slab must split evenly");
       const float* Wz = a.lv.Wz[0];
@@ -810,7 +832,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
     }
     __syncthreads();
     for (int l = 1; l + 1 < a.levels; ++l) {
-      const int wf = M >> l, sf = wf + 1, hf = wf >> 1, wc = wf >> 1, hc = wc >> 1, sc = wc + 1;
+      const int wf = M >> l, sf = wf + 1, hf = wf / C, wc = wf >> 1, hc = wc / C, sc = wc + 1;
       const float* Wz = a.lv.Wz[l];
       const float2* WR = a.lv.WR[l];
       for (int p = tid; p < hc * wc; p += NT) {
@@ -831,7 +853,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
     }
     {  // coarsest level: correction c = G (R - Q z), stored over z
       const int l = a.levels - 1;
-      const int wl = M >> l, hl = wl >> 1, sl = wl + 1;
+      const int wl = M >> l, hl = wl / C, sl = wl + 1;
       const float2* G = a.lv.G[l];
       const float2* Q = a.lv.Q[l];
       for (int p = tid; p < hl * wl; p += NT) {
@@ -847,7 +869,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
         fill_halo(l + 1);
       }
       __syncthreads();
-      const int wl = M >> l, hl = wl >> 1, sl = wl + 1, wc = wl >> 1, sc = wc + 1;
+      const int wl = M >> l, hl = wl / C, sl = wl + 1, wc = wl >> 1, sc = wc + 1;
       const float2* G = a.lv.G[l];
       const float2* Q = a.lv.Q[l];
 #pragma unroll 4
@@ -911,16 +933,294 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Step2Threads<M>::val
   }
   if (a.verify) {
     const double part = 0.5 * block_sum_f<NT>(acc_after, redf, redd);
-    if (tid == 0) {
-      xd2[rank] = part;
-      *cl.map_shared_rank(&xd2[rank], peer) = part;
+    if (tid == 0) cluster_publish<C>(cl, rank, xd2, part);
+  }
+  cl.sync();  // neighbours may still read my coarse rows; also publishes xd2
+  if (rank == 0 && tid == 0) {
+    double phi = 0.0, after = 0.0;
+#pragma unroll
+    for (int d = 0; d < C; ++d) {
+      phi += xd[d];
+      after += xd2[d];
+    }
+    a.mu[kb] = mu;
+    a.phi[kb] = phi * (0.5 / (double)(M * M));
+    if (a.verify) a.phi_after[kb] = after;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward transform of one tile per cluster (any m): modes
+//   0 misfit partial (1/2 m^2) sum (|F psi| - a_k)^2 per position,
+//   1 intensity |F psi|^2 in natural order,
+//   2 F x of a natural-order tile.
+template <int M, int C, int MODE>
+__global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_fwdc(const FwdArgs a) {
+  using TL = CTile<M, C>;
+  constexpr int NT = TL::NT, H = TL::H, SR = TL::SR, SC = TL::SC, N1 = TL::N1, N2 = TL::N2;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  extern __shared__ float2 sm[];
+  float2* rowbuf = sm;
+  float2* colbuf = sm + H * SR;
+  __shared__ double xd[C];
+  __shared__ double redd[2];
+  __shared__ float redf[NT / 32];
+  const int tid = threadIdx.x;
+  const int t = blockIdx.x / C;
+  const int row0 = rank * H;
+  cl.barrier_arrive();
+  if (MODE == 2) {
+    const float2* x = a.in + (size_t)t * M * M;
+    for (int p = tid; p < H * M; p += NT) rowbuf[(p / M) * SR + p % M] = x[row0 * M + p];
+  } else {
+    const int o_r = a.pos[2 * t], o_c = a.pos[2 * t + 1];
+    for (int p = tid; p < H * M; p += NT) {
+      const int lr = p / M, c = p % M, r = row0 + lr;
+      rowbuf[lr * SR + c] = cmul(a.probe[r * M + c], gather_obj(a.object, a.n_rows, a.n_cols, o_r + r, o_c + c));
     }
   }
-  cl.sync();  // the peer may still read my coarse rows; also publishes xd2
+  __syncthreads();
+  gpass_a_fwd<M, H, SR, 1, NT>(rowbuf, tid);
+  __syncthreads();
+  gpass_b<M, H, SR, 1, NT, false>(rowbuf, tid);
+  __syncthreads();
+  cl.barrier_wait();
+  cluster_rows_to_cols<M, C>(cl, rank, rowbuf, colbuf, tid);
+  cl.sync();
+  gpass_a_fwd<M, H, 1, SC, NT>(colbuf, tid);
+  __syncthreads();
+  gpass_b<M, H, 1, SC, NT, false>(colbuf, tid);
+  __syncthreads();
+  float acc = 0.f;
+  for (int p = tid; p < M * H; p += NT) {
+    const int er = p / H, lc = p % H, ec = rank * H + lc;
+    const float2 v = colbuf[er * SC + lc];
+    const size_t nat = (size_t)storage_to_freq<M>(er) * M + storage_to_freq<M>(ec);
+    if (MODE == 0) {
+      const float dm = sqrtf(cabs2(v)) - a.amp[(size_t)t * M * M + er * M + ec];
+      acc = fmaf(dm, dm, acc);
+    } else if (MODE == 1) {
+      a.out_intensity[(size_t)t * M * M + nat] = cabs2(v);
+    } else {
+      a.out[(size_t)t * M * M + nat] = v;
+    }
+  }
+  if (MODE == 0) {
+    const double part = block_sum_f<NT>(acc, redf, redd);
+    if (tid == 0) cluster_publish<C>(cl, rank, xd, part);
+    cl.sync();
+    if (rank == 0 && tid == 0) {
+      double tot = 0.0;
+#pragma unroll
+      for (int d = 0; d < C; ++d) tot += xd[d];
+      a.partial[t] = tot * (0.5 / (double)(M * M));
+    }
+  }
+}
+
+// Inverse 2-D DFT (with 1/m^2) of natural-order tiles, one tile per cluster.
+template <int M, int C>
+__global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_ifftc(const FwdArgs a) {
+  using TL = CTile<M, C>;
+  constexpr int NT = TL::NT, H = TL::H, SR = TL::SR, SC = TL::SC;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  extern __shared__ float2 sm[];
+  float2* rowbuf = sm;
+  float2* colbuf = sm + H * SR;
+  const int tid = threadIdx.x;
+  const int t = blockIdx.x / C;
+  const float2* x = a.in + (size_t)t * M * M;
+  const float sc = 1.f / (float)(M * M);
+  cl.barrier_arrive();
+  for (int p = tid; p < M * H; p += NT) {
+    const int er = p / H, lc = p % H, ec = rank * H + lc;
+    colbuf[er * SC + lc] = cscale(x[(size_t)storage_to_freq<M>(er) * M + storage_to_freq<M>(ec)], sc);
+  }
+  __syncthreads();
+  gpass_b<M, H, 1, SC, NT, true>(colbuf, tid);
+  __syncthreads();
+  gpass_a_inv<M, H, 1, SC, NT>(colbuf, tid);
+  __syncthreads();
+  cl.barrier_wait();
+  cluster_cols_to_rows<M, C>(cl, rank, colbuf, rowbuf, tid);
+  cl.sync();
+  gpass_b<M, H, SR, 1, NT, true>(rowbuf, tid);
+  __syncthreads();
+  gpass_a_inv<M, H, SR, 1, NT>(rowbuf, tid);
+  __syncthreads();
+  float2* y = a.out + (size_t)t * M * M + rank * H * M;
+  for (int p = tid; p < H * M; p += NT) y[p] = rowbuf[(p / M) * SR + p % M];
+}
+
+// ---------------------------------------------------------------------------
+// Wirtinger gradient of the exit-wave misfit per position (Sec. 2.1), with the
+// revised exit wave recomputed: forward FFT, modulus replacement, inverse FFT,
+// then gz = conj(Q) (psi - R), gq = conj(z_k) (psi - R) on the patch.
+template <int M, int C>
+__global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_gradc(const GradArgs a) {
+  using TL = CTile<M, C>;
+  constexpr int NT = TL::NT, H = TL::H, SR = TL::SR, SC = TL::SC, N1 = TL::N1, N2 = TL::N2, SLOTS = TL::SLOTS;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  extern __shared__ float2 sm[];
+  float2* rowbuf = sm;
+  float2* colbuf = sm + H * SR;
+  float2* zbuf = colbuf + M * SC;
+  __shared__ double xd[C];
+  __shared__ double redd[2];
+  __shared__ float redf[NT / 32];
+  const int tid = threadIdx.x;
+  const int kb = blockIdx.x / C;
+  const int k = a.first + kb;
+  const int o_r = a.pos[2 * k], o_c = a.pos[2 * k + 1];
+  const int row0 = rank * H;
+  cl.barrier_arrive();
+  for (int p = tid; p < H * M; p += NT) {
+    const int lr = p / M, c = p % M, r = row0 + lr;
+    const float2 zk = gather_obj(a.object, a.n_rows, a.n_cols, o_r + r, o_c + c);
+    zbuf[p] = zk;
+    rowbuf[lr * SR + c] = cmul(a.probe[r * M + c], zk);
+  }
+  __syncthreads();
+  gpass_a_fwd<M, H, SR, 1, NT>(rowbuf, tid);
+  __syncthreads();
+  gpass_b<M, H, SR, 1, NT, false>(rowbuf, tid);
+  __syncthreads();
+  cl.barrier_wait();
+  cluster_rows_to_cols<M, C>(cl, rank, rowbuf, colbuf, tid);
+  cl.sync();
+  gpass_a_fwd<M, H, 1, SC, NT>(colbuf, tid);
+  __syncthreads();
+  const float* amp = a.amp + (size_t)k * M * M + rank * H;
+  const float inv_m2 = 1.f / (float)(M * M);
+  float acc = 0.f;
+#pragma unroll
+  for (int t = 0; t < SLOTS; ++t) {
+    const int s = tid + t * NT, k2 = s / H, lc = s % H;
+    float2 v[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) v[i] = colbuf[(i + N1 * k2) * SC + lc];
+    Dft<N1, false>::run(v);
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      const float am = amp[(i + N1 * k2) * M + lc];
+      const float p2 = cabs2(v[i]);
+      if (p2 > 0.f) {
+        const float inv = rsqrtf(p2);
+        const float dm = fmaf(p2, inv, -am);
+        acc = fmaf(dm, dm, acc);
+        v[i] = cscale(v[i], am * inv * inv_m2);
+      } else {
+        acc = fmaf(am, am, acc);
+        v[i] = make_float2(am * inv_m2, 0.f);
+      }
+    }
+    Dft<N1, true>::run(v);
+#pragma unroll
+    for (int i = 0; i < N1; ++i) colbuf[(i + N1 * k2) * SC + lc] = v[i];
+  }
+  __syncthreads();
+  gpass_a_inv<M, H, 1, SC, NT>(colbuf, tid);
+  const double phi_part = block_sum_f<NT>(acc, redf, redd);
+  cluster_cols_to_rows<M, C>(cl, rank, colbuf, rowbuf, tid);
+  if (tid == 0) cluster_publish<C>(cl, rank, xd, phi_part);
+  cl.sync();
+  gpass_b<M, H, SR, 1, NT, true>(rowbuf, tid);
+  __syncthreads();
+  gpass_a_inv<M, H, SR, 1, NT>(rowbuf, tid);
+  __syncthreads();
+  float2* gz = a.gz + (size_t)kb * M * M;
+  float2* gq = a.gq + (size_t)kb * M * M;
+  for (int p = tid; p < H * M; p += NT) {
+    const int lr = p / M, c = p % M, r = row0 + lr;
+    const float2 zk = zbuf[p];
+    const float2 q = a.probe[r * M + c];
+    const float2 e = csub(cmul(q, zk), rowbuf[lr * SR + c]);
+    gz[r * M + c] = cconjmul(q, e);
+    gq[r * M + c] = cconjmul(zk, e);
+  }
   if (rank == 0 && tid == 0) {
-    a.mu[kb] = mu;
-    a.phi[kb] = (xd[0] + xd[1]) * (0.5 / (double)(M * M));
-    if (a.verify) a.phi_after[kb] = xd2[0] + xd2[1];
+    double tot = 0.0;
+#pragma unroll
+    for (int d = 0; d < C; ++d) tot += xd[d];
+    a.phi[kb] = tot * (0.5 / (double)(M * M));
+  }
+}
+
+// Object gradient sum_k P_k^T gz_k over 16 x 16 tiles and probe gradient
+// sum_k gq_k, each in position order (deterministic); optionally added to the
+// existing values (later chunks of positions).
+__global__ void __launch_bounds__(kApplyThreads) k_grad_reduce(const GradReduceArgs a) {
+  extern __shared__ int glist[];
+  __shared__ int warp_count[kApplyThreads / 32];
+  __shared__ int total;
+  __shared__ float2 part_s[kApplyProbeGroups][32];
+  const int tid = threadIdx.x;
+  const int n_tiles = a.tiles_x * a.tiles_y;
+  const int m = a.m;
+  const size_t mm = (size_t)m * m;
+  if ((int)blockIdx.x < n_tiles) {
+    if (!a.grad_object) return;
+    const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x % a.tiles_x;
+    const int r0 = ty * kApplyTile, c0 = tx * kApplyTile;
+    if (tid == 0) total = 0;
+    __syncthreads();
+    for (int base = 0; base < a.b; base += kApplyThreads) {
+      const int kb = base + tid;
+      int pr = 0, pc = 0;
+      bool hit = false;
+      if (kb < a.b) {
+        pr = a.pos[2 * (a.first + kb)];
+        pc = a.pos[2 * (a.first + kb) + 1];
+        hit = pr < r0 + kApplyTile && pr + m > r0 && pc < c0 + kApplyTile && pc + m > c0;
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, hit);
+      const int lane = tid & 31, warp = tid >> 5;
+      if (lane == 0) warp_count[warp] = __popc(mask);
+      __syncthreads();
+      int off = total;
+      for (int w = 0; w < warp; ++w) off += warp_count[w];
+      if (hit) {
+        const int slot = off + __popc(mask & ((1u << lane) - 1u));
+        glist[3 * slot] = kb;
+        glist[3 * slot + 1] = pr;
+        glist[3 * slot + 2] = pc;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        int t = total;
+        for (int w = 0; w < kApplyThreads / 32; ++w) t += warp_count[w];
+        total = t;
+      }
+      __syncthreads();
+    }
+    const int cnt = total;
+    const int row = r0 + tid / kApplyTile, col = c0 + tid % kApplyTile;
+    if (row >= a.n_rows || col >= a.n_cols) return;
+    float2 g = czero();
+    for (int t = 0; t < cnt; ++t) {
+      const int lr = row - glist[3 * t + 1], lc = col - glist[3 * t + 2];
+      if ((unsigned)lr < (unsigned)m && (unsigned)lc < (unsigned)m)
+        g = cadd(g, a.gz[(size_t)glist[3 * t] * mm + lr * m + lc]);
+    }
+    const size_t gi = (size_t)row * a.n_cols + col;
+    a.grad_object[gi] = a.accumulate ? cadd(a.grad_object[gi], g) : g;
+  } else {
+    if (!a.grad_probe) return;
+    const int lane = tid & 31, g = tid >> 5;
+    const int p = (blockIdx.x - n_tiles) * 32 + lane;
+    float2 sum = czero();
+    if (p < (int)mm)
+      for (int kb = g; kb < a.b; kb += kApplyProbeGroups) sum = cadd(sum, a.gq[(size_t)kb * mm + p]);
+    part_s[g][lane] = sum;
+    __syncthreads();
+    if (g != 0 || p >= (int)mm) return;
+    float2 tot = part_s[0][lane];
+#pragma unroll
+    for (int i = 1; i < kApplyProbeGroups; ++i) tot = cadd(tot, part_s[i][lane]);
+    a.grad_probe[p] = a.accumulate ? cadd(a.grad_probe[p], tot) : tot;
   }
 }
 
@@ -1304,6 +1604,8 @@ size_t step_smem_bytes(int m, int levels) {
   }
 }
 
+cudaError_t set_cluster_attrs();
+
 cudaError_t upload_twiddles() {
   float2 h[256];
   for (int t = 0; t < 256; ++t) {
@@ -1319,12 +1621,16 @@ cudaError_t upload_twiddles() {
   if ((e = set_step_smem<32>()) != cudaSuccess) return e;
   if ((e = set_step_smem<64>()) != cudaSuccess) return e;
   if ((e = set_step_smem<128>()) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_step2<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(step2_smem_elems<64>() * sizeof(float2)))) != cudaSuccess)
+  if ((e = cudaFuncSetAttribute(k_stepc<64, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(CTile<64, 2>::smem_elems * sizeof(float2)))) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(k_step2<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(step2_smem_elems<128>() * sizeof(float2)))) != cudaSuccess)
+  if ((e = cudaFuncSetAttribute(k_stepc<128, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(CTile<128, 2>::smem_elems * sizeof(float2)))) != cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(k_stepc<256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(CTile<256, 8>::smem_elems * sizeof(float2)))) != cudaSuccess)
+    return e;
+  if ((e = set_cluster_attrs()) != cudaSuccess) return e;
   if ((e = set_aux_smem<16>()) != cudaSuccess) return e;
   if ((e = set_aux_smem<32>()) != cudaSuccess) return e;
   if ((e = set_aux_smem<64>()) != cudaSuccess) return e;
@@ -1344,6 +1650,7 @@ cudaError_t launch_amp_prep(const float* d, float* amp, int m, int n_pos, cudaSt
     case 32: k_amp_prep<32><<<blocks, 256, 0, s>>>(d, amp, n_pos); break;
     case 64: k_amp_prep<64><<<blocks, 256, 0, s>>>(d, amp, n_pos); break;
     case 128: k_amp_prep<128><<<blocks, 256, 0, s>>>(d, amp, n_pos); break;
+    case 256: k_amp_prep<256><<<blocks, 256, 0, s>>>(d, amp, n_pos); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1379,17 +1686,115 @@ cudaError_t launch_probe_max(const float2* probe, int m, unsigned* slot, cudaStr
   return cudaGetLastError();
 }
 
+// Launch of a C-CTA cluster kernel with programmatic stream serialisation.
+template <typename Kernel, typename... Args>
+cudaError_t launch_cluster_pdl(Kernel kernel, int cluster, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                               Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = cluster;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <typename Kernel, typename... Args>
+cudaError_t launch_cluster_plain(Kernel kernel, int cluster, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                 Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <int M, int MODE>
+cudaError_t launch_fwdc_t(int count, const FwdArgs& a, cudaStream_t s) {
+  constexpr int C = ClusterSize<M>::value;
+  using TL = CTile<M, C>;
+  cudaError_t e = launch_cluster_plain(k_fwdc<M, C, MODE>, C, dim3(C * count), dim3(TL::NT),
+                                       TL::smem_elems * sizeof(float2), s, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 template <int M>
-cudaError_t launch_step2_t(int b, const StepArgs& a, cudaStream_t s) {
-  cudaError_t e = launch_pdl(k_step2<M>, dim3(2 * b), dim3(Step2Threads<M>::value),
-                             step2_smem_elems<M>() * sizeof(float2), s, a);
+cudaError_t launch_ifftc_t(int count, const FwdArgs& a, cudaStream_t s) {
+  constexpr int C = ClusterSize<M>::value;
+  using TL = CTile<M, C>;
+  cudaError_t e = launch_cluster_plain(k_ifftc<M, C>, C, dim3(C * count), dim3(TL::NT),
+                                       TL::smem_elems * sizeof(float2), s, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_gradc_t(int b, const GradArgs& a, cudaStream_t s) {
+  constexpr int C = ClusterSize<M>::value;
+  using TL = CTile<M, C>;
+  cudaError_t e = launch_cluster_plain(k_gradc<M, C>, C, dim3(C * b), dim3(TL::NT),
+                                       TL::smem_elems * sizeof(float2), s, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <typename Kernel>
+cudaError_t set_cluster_smem(Kernel k, size_t elems) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(elems * sizeof(float2)));
+}
+
+template <int M>
+cudaError_t set_grad_attrs() {
+  constexpr int C = ClusterSize<M>::value;
+  return set_cluster_smem(k_gradc<M, C>, CTile<M, C>::smem_elems);
+}
+
+// Dynamic shared-memory limits of the cluster kernels (once per device).
+cudaError_t set_cluster_attrs() {
+  cudaError_t e;
+  if ((e = set_cluster_smem(k_fwdc<256, 8, 0>, CTile<256, 8>::smem_elems)) != cudaSuccess) return e;
+  if ((e = set_cluster_smem(k_fwdc<256, 8, 1>, CTile<256, 8>::smem_elems)) != cudaSuccess) return e;
+  if ((e = set_cluster_smem(k_fwdc<256, 8, 2>, CTile<256, 8>::smem_elems)) != cudaSuccess) return e;
+  if ((e = set_cluster_smem(k_ifftc<256, 8>, CTile<256, 8>::smem_elems)) != cudaSuccess) return e;
+  if ((e = set_grad_attrs<16>()) != cudaSuccess) return e;
+  if ((e = set_grad_attrs<32>()) != cudaSuccess) return e;
+  if ((e = set_grad_attrs<64>()) != cudaSuccess) return e;
+  if ((e = set_grad_attrs<128>()) != cudaSuccess) return e;
+  if ((e = set_grad_attrs<256>()) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_grad_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024)) !=
+      cudaSuccess)
+    return e;
+  return cudaSuccess;
+}
+
+template <int M>
+cudaError_t launch_stepc_t(int b, const StepArgs& a, cudaStream_t s) {
+  constexpr int C = ClusterSize<M>::value;
+  using TL = CTile<M, C>;
+  cudaError_t e = launch_cluster_pdl(k_stepc<M, C>, C, dim3(C * b), dim3(TL::NT), TL::smem_elems * sizeof(float2),
+                                     s, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_step(int m, int b, const StepArgs& a, cudaStream_t s) {
-  if (m == 128) return launch_step2_t<128>(b, a, s);
-  if (m == 64) return launch_step2_t<64>(b, a, s);
+  if (m == 256) return launch_stepc_t<256>(b, a, s);
+  if (m == 128) return launch_stepc_t<128>(b, a, s);
+  if (m == 64) return launch_stepc_t<64>(b, a, s);
   EMG_DISPATCH_M(m, (launch_step_t<M>(b, a, s)));
 }
 
@@ -1405,6 +1810,17 @@ cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
 cudaError_t launch_misfit(int m, const float2* object, const float2* probe, const int32_t* pos,
                           const float* amp, int n_rows, int n_cols, int n_pos, double* partial,
                           cudaStream_t s) {
+  if (m == 256) {
+    FwdArgs f{};
+    f.object = object;
+    f.probe = probe;
+    f.pos = pos;
+    f.amp = amp;
+    f.n_rows = n_rows;
+    f.n_cols = n_cols;
+    f.partial = partial;
+    return launch_fwdc_t<256, 0>(n_pos, f, s);
+  }
   EMG_DISPATCH_M(m, (launch_misfit_t<M>(object, probe, pos, amp, n_rows, n_cols, n_pos, partial, s)));
 }
 
@@ -1415,12 +1831,59 @@ cudaError_t launch_sum(const double* x, int n, double scale, double* out, cudaSt
 
 cudaError_t launch_simulate(int m, const float2* object, const float2* probe, const int32_t* pos,
                             int n_rows, int n_cols, int n_pos, float* out, cudaStream_t s) {
+  if (m == 256) {
+    FwdArgs f{};
+    f.object = object;
+    f.probe = probe;
+    f.pos = pos;
+    f.n_rows = n_rows;
+    f.n_cols = n_cols;
+    f.out_intensity = out;
+    return launch_fwdc_t<256, 1>(n_pos, f, s);
+  }
   EMG_DISPATCH_M(m, (launch_simulate_t<M>(object, probe, pos, n_rows, n_cols, n_pos, out, s)));
 }
 
 cudaError_t launch_fft2(int m, const float2* in, float2* out, int count, int inverse,
                         cudaStream_t s) {
+  if (m == 256) {
+    FwdArgs f{};
+    f.in = in;
+    f.out = out;
+    return inverse ? launch_ifftc_t<256>(count, f, s) : launch_fwdc_t<256, 2>(count, f, s);
+  }
   EMG_DISPATCH_M(m, (launch_fft2_t<M>(in, out, count, inverse, s)));
+}
+
+cudaError_t launch_gradient(int m, int b, const GradArgs& a, cudaStream_t s) {
+  switch (m) {
+    case 16: return launch_gradc_t<16>(b, a, s);
+    case 32: return launch_gradc_t<32>(b, a, s);
+    case 64: return launch_gradc_t<64>(b, a, s);
+    case 128: return launch_gradc_t<128>(b, a, s);
+    case 256: return launch_gradc_t<256>(b, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t s) {
+  const int n_tiles = a.tiles_x * a.tiles_y;
+  const int n_probe = (a.m * a.m + 31) / 32;
+  k_grad_reduce<<<n_tiles + n_probe, kApplyThreads, (size_t)a.b * 3 * sizeof(int), s>>>(a);
+  return cudaGetLastError();
+}
+
+// Whether the step kernel for probe side m supports `levels` multigrid levels.
+bool step_supported(int m, int levels) {
+  if (m <= 32) return step_smem_bytes(m, levels) <= (size_t)step_smem_limit();
+  const int C = (m == 256) ? 8 : 2;
+  if ((m >> (levels - 1)) < C) return false;  // every CTA needs a row at the coarsest level
+  size_t need = 0;
+  for (int l = 1; l < levels; ++l) {
+    const size_t wl = (size_t)m >> l, hl = wl / C;
+    need += (2 * hl + 2) * (wl + 1);
+  }
+  return need <= (size_t)m * (m / C + 1);
 }
 
 cudaError_t launch_normalize_probe(const float* amp, int m, int n_pos, float2* probe,
@@ -1540,7 +2003,7 @@ extern "C" emg_status emg_step_minibatch_noalloc(float* object, int32_t n_rows, 
   using namespace emg;
   if (!object || !probe || !pos || !intensity || !idx || !p) return EMG_EINVAL;
   if (n_rows < 1 || n_cols < 1 || n_pos < 1 || b < 1 || b > n_pos) return EMG_EINVAL;
-  if (m != 16 && m != 32 && m != 64 && m != 128) return EMG_ENOTSUP;
+  if (m != 16 && m != 32 && m != 64 && m != 128) return EMG_ENOTSUP;  // m = 256 needs a cluster
   if (!(p->alpha > 0.f) || !isfinite(p->alpha) || !(p->w_eps >= 0.f) || !isfinite(p->w_eps))
     return EMG_EINVAL;
   if (p->levels < 1 || p->levels > kMaxLevels || (m >> (p->levels - 1)) < 2) return EMG_EINVAL;

@@ -79,7 +79,7 @@ def test_create_rejects_bad_problems(lib):
     ctx = ctypes.c_void_p()
     for prob, expect in [
         (emg.EmgProblem(64, 64, 48, 4, 0x1000, 0x2000), emg.EMG_ENOTSUP),
-        (emg.EmgProblem(64, 64, 256, 4, 0x1000, 0x2000), emg.EMG_ENOTSUP),
+        (emg.EmgProblem(64, 64, 512, 4, 0x1000, 0x2000), emg.EMG_ENOTSUP),
         (emg.EmgProblem(0, 64, 32, 4, 0x1000, 0x2000), emg.EMG_EINVAL),
         (emg.EmgProblem(64, 64, 32, 0, 0x1000, 0x2000), emg.EMG_EINVAL),
         (emg.EmgProblem(64, 64, 32, 4, 0, 0x2000), emg.EMG_EINVAL),

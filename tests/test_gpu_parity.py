@@ -31,7 +31,7 @@ def torch():
 
 # ----------------------------------------------------------------- FFT
 
-@pytest.mark.parametrize("m", [16, 32, 64, 128])
+@pytest.mark.parametrize("m", [16, 32, 64, 128, 256])
 def test_fft2_forward_inverse_match_the_dft(lib, torch, m):
     rng = np.random.default_rng(m)
     x = (rng.standard_normal((3, m, m)) + 1j * rng.standard_normal((3, m, m))).astype(np.complex64)
@@ -50,7 +50,7 @@ def test_fft2_forward_inverse_match_the_dft(lib, torch, m):
     assert rel_err(yd.cpu().numpy(), O.idft2(x.astype(np.complex128))) < 2e-6
 
 
-@pytest.mark.parametrize("m", [16, 32, 64, 128])
+@pytest.mark.parametrize("m", [16, 32, 64, 128, 256])
 def test_simulated_intensities_match_the_forward_model(lib, torch, m):
     case = Case(n=2 * m + 24, m=m, side=3)
     out = torch.empty((case.n_pos, m, m), dtype=torch.float32, device="cuda")
@@ -66,7 +66,7 @@ def test_simulated_intensities_match_the_forward_model(lib, torch, m):
         assert rel_err(got[k], ref[k]) < 1e-5, k
 
 
-@pytest.mark.parametrize("m", [32, 128])
+@pytest.mark.parametrize("m", [32, 128, 256])
 def test_misfit_matches_the_oracle(lib, torch, m):
     case = Case(n=2 * m + 16, m=m, side=4, noise_peak=1e4)
     p = oracle_params()
@@ -105,6 +105,8 @@ STEP_CASES = [
     (128, 1, "const", True, "wavg", 6),
     (128, 3, "bilinear", True, "wavg", 6),
     (128, 7, "const", True, "wavg", 3),
+    (256, 1, "const", True, "wavg", 4),
+    (256, 3, "bilinear", True, "wavg", 4),
 ]
 
 

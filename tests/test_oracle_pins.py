@@ -505,3 +505,17 @@ def test_fifty_epoch_trajectory_is_sensitive_at_rounding_level():
     m2 = np.array([h["misfit"] for h in h2])
     assert np.max(np.abs(m2 - m1) / m1) > 1e-3
     assert m1[-1] < 1e-2 * m1[0] * 10   # while the run itself converges
+
+
+def test_whole_object_gradient_matches_central_differences():
+    """The summed gradients of Phi over all positions (Sec. 2.1) against FD."""
+    z_true, Q_true, pos, a = _tiny_workload(1, m=8, n=20, side=3, step=4)
+    rng = np.random.default_rng(1100)
+    z = synth.perturb(z_true, 0.3, rng)
+    Q = synth.perturb(Q_true, 0.3, rng)
+    phi, gz, gq = O.misfit_gradients(Q, z, pos, a)
+    assert np.isclose(phi, O.misfit(Q, z, pos, a), rtol=1e-13)
+    fz = _fd_wirtinger(lambda zz: O.misfit(Q, zz, pos, a), z, h=1e-6)
+    fq = _fd_wirtinger(lambda qq: O.misfit(qq, z, pos, a), Q, h=1e-6)
+    assert np.max(np.abs(gz - fz)) < 1e-5 * np.max(np.abs(gz))
+    assert np.max(np.abs(gq - fq)) < 1e-5 * np.max(np.abs(gq))
