@@ -52,6 +52,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "grad_n1024_m256", "batch64"],
+                    help="mg_n512_m128: eMAGPIE epochs (default); grad_n1024_m256: exit-wave "
+                         "misfit gradient over all positions; batch64: 64 uneven reconstructions, "
+                         "one graph launch per epoch")
     return ap.parse_args()
 
 
@@ -377,11 +382,233 @@ def run_gpu(args, world, rank, local):
     ctx.close()
 
 
+def run_gpu_grad(args, world, rank, local):
+    """One step = Phi and its Wirtinger gradients over all positions (Sec. 2.1)."""
+    import torch
+
+    import paper_2511_01793_gb300 as emg
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    emg.build()
+    emg.load()
+    w = synth.make_workload(args.workload)
+    p = w.params
+    m, N, B = p["m"], len(w.pos), p["minibatch"]
+    d = host_intensities(w, rank)
+    rng = np.random.default_rng(rank)
+    z0 = synth.perturb(w.z_true, 0.2, rng).astype(np.complex64)
+    q0 = synth.perturb(w.q_true, 0.2, rng).astype(np.complex64)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = emg.Context(w.pos, d, p["n"], p["n"], emg.emg_default_params(alpha=p["alpha"], minibatch=B),
+                          stream=stream)
+        zd = torch.from_numpy(z0).cuda()
+        qd = torch.from_numpy(q0).cuda()
+        gz = torch.empty_like(zd)
+        gq = torch.empty_like(qd)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+        def step():
+            emg.emg_misfit_gradient(ctx.ctx, zd.data_ptr(), qd.data_ptr(), gz.data_ptr(), gq.data_ptr(), False)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        emg.emg_profile_read(ctx.ctx)
+        clocks = ClockSampler(local)
+        clocks.start()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        counts = emg.emg_profile_read(ctx.ctx)
+        total_ms = sum(a.elapsed_time(b) for a, b in ev)
+        # gradient-kernel share: time the chunk kernels alone in a second pass
+        gms = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            emg.emg_misfit_gradient(ctx.ctx, zd.data_ptr(), qd.data_ptr(), 0, 0, False)
+            a1.record(stream)
+            gms.append((a0, a1))
+        torch.cuda.synchronize()
+        grad_only_ms = sum(a.elapsed_time(b) for a, b in gms) / args.steps
+        # end to end: pinned host state in, gradients and misfit out
+        zh = torch.from_numpy(z0).pin_memory()
+        qh = torch.from_numpy(q0).pin_memory()
+        gzh = torch.empty_like(zh).pin_memory()
+        gqh = torch.empty_like(qh).pin_memory()
+        t_e2e = 0.0
+        for i in range(args.steps + 1):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            zd.copy_(zh, non_blocking=True)
+            qd.copy_(qh, non_blocking=True)
+            emg.emg_misfit_gradient(ctx.ctx, zd.data_ptr(), qd.data_ptr(), gz.data_ptr(), gq.data_ptr(), True)
+            gzh.copy_(gz, non_blocking=True)
+            gqh.copy_(gq, non_blocking=True)
+            torch.cuda.synchronize()
+            if i > 0:
+                t_e2e += time.perf_counter() - t0
+    value = world * N * args.steps / (total_ms / 1e3)
+    alg = 28 * m * m          # patch read 8m^2 + amplitude 4m^2 + two gradient patches 16m^2
+    achieved = alg * N / (grad_only_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    line = {
+        "metric": "scan positions/sec per misfit-gradient evaluation", "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: object {p['n']}^2, probe {m}^2, {N} positions, chunks of {B}",
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "e2e": {"value": world * N * args.steps / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": int(z0.nbytes + q0.nbytes),
+                "d2h_bytes_per_step": int(z0.nbytes + q0.nbytes + 8)},
+        "gpu_launches": sum(v[1] for v in counts.values()),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 5), "peak_source": peak_kind, "traffic": None,
+                     "kernel": f"k_gradc<{m}> (+ its sums)",
+                     "algorithmic_bytes_per_launch": int(alg * B),
+                     "timing": f"misfit-only gradient kernels {grad_only_ms:.3f} ms per step"},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+
+        t0 = time.perf_counter()
+        done = 0
+        zz, qq = z0.astype(np.complex128), q0.astype(np.complex128)
+        a = np.sqrt(np.maximum(d.astype(np.float64), 0.0))
+        while done < N and time.perf_counter() - t0 < args.cpu_seconds:
+            O.misfit_gradients(qq, zz, w.pos[done:done + 8], a[done:done + 8])
+            done += 8
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"gradients of {done} positions, {dt:.1f} s single-thread FP64"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def batch_problems(count: int = 64, seed: int = 1003):
+    """64 uneven problems: object side from {256, 512, 768, 1024}, probe side from
+    {64, 128, 256} with m <= n/2, 100-2500 positions (raster step m/8, +-2 px
+    jitter, capped by the raster that fits), Poisson peak 1e3-1e5 (log-uniform),
+    2 or 3 multigrid levels."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    probs = []
+    for i in range(count):
+        n = int(rng.choice([256, 512, 768, 1024]))
+        m = int(rng.choice([mm for mm in (64, 128, 256) if mm <= n // 2]))
+        step = m // 8
+        side_fit = (n - m) // step + 1
+        side = max(10, min(int(np.sqrt(rng.integers(100, 2501))), side_fit))
+        probs.append(dict(n=n, m=m, side=side, step=step, jitter=2, peak=float(10 ** rng.uniform(3, 5)),
+                          levels=int(rng.choice([2, 3])), seed=seed * 1000 + i))
+    return probs
+
+
+def run_gpu_batch(args, world, rank, local):
+    import torch
+
+    import paper_2511_01793_gb300 as emg
+
+    torch.cuda.set_device(local)
+    emg.build()
+    emg.load()
+    probs = batch_problems()
+    stream = torch.cuda.Stream()
+    ctxs, total_pos, alg_bytes, tiles = [], 0, 0, {}
+    gen = torch.Generator(device="cuda")
+    with torch.cuda.stream(stream):
+        for pr in probs:
+            rng = np.random.Generator(np.random.PCG64(pr["seed"] + rank))
+            n, m = pr["n"], pr["m"]
+            z_true = synth.make_object(n, n, rng, phi_max=math.pi).astype(np.complex64)
+            q_true = synth.make_probe(m, radius=m * 10.0 / 32.0)
+            pos = synth.make_scan(n, m, pr["side"], pr["step"], pr["jitter"], rng)
+            N = len(pos)
+            zt = torch.from_numpy(z_true).cuda()
+            qt = torch.from_numpy(q_true.astype(np.complex64)).cuda()
+            pt = torch.from_numpy(pos).cuda()
+            d = torch.empty((N, m, m), dtype=torch.float32, device="cuda")
+            emg.emg_simulate_intensity(zt.data_ptr(), n, n, qt.data_ptr(), m, pt.data_ptr(), N, d.data_ptr(),
+                                       stream.cuda_stream)
+            gen.manual_seed(pr["seed"] + rank)
+            scale = pr["peak"] / float(d.reshape(N, -1).amax(dim=1).mean())
+            d = torch.poisson(d * scale, generator=gen) / scale
+            params = emg.emg_default_params(alpha=0.05, levels=pr["levels"], minibatch=min(64, N),
+                                            prolong=emg.EMG_PROLONG_BILINEAR, seed=pr["seed"])
+            ctx = emg.Context(pos, d, n, n, params, obj=torch.ones((n, n), dtype=torch.complex64),
+                              probe=torch.from_numpy(synth.blur_probe(q_true, 2.0).astype(np.complex64)),
+                              stream=stream)
+            emg.emg_normalize_probe(ctx.ctx)
+            chosen, _ = emg.emg_autotune(ctx.ctx)
+            tiles[f"m{m}"] = tiles.get(f"m{m}", []) + [chosen]
+            del ctx.intensity
+            ctxs.append(ctx)
+            total_pos += N
+            alg_bytes += 20 * m * m * N
+        batch = emg.emg_batch_create([c.ctx for c in ctxs])
+        for _ in range(args.warmup):
+            emg.emg_batch_run_epochs(batch, 1, stream.cuda_stream)
+        torch.cuda.synchronize()
+        for c in ctxs:
+            emg.emg_profile_read(c.ctx)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        clocks.start()
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            emg.emg_batch_run_epochs(batch, 1, stream.cuda_stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        total_ms = sum(a.elapsed_time(b) for a, b in ev)
+        launches = sum(sum(v[1] for v in emg.emg_profile_read(c.ctx).values()) for c in ctxs)
+        emg.emg_batch_destroy(batch)
+    value = total_pos * args.steps / (total_ms / 1e3)
+    achieved = alg_bytes * args.steps / (total_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    line = {
+        "metric": "scan positions/sec per epoch over a batch of reconstructions", "value": value, "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch64: {len(probs)} problems, {total_pos} positions per epoch, object "
+                               "256-1024, probe 64-256, 2-3 levels, one graph launch per epoch",
+                   "l2": f"inputs {alg_bytes / 2.5e9:.1f} GB of amplitudes and patches, larger than L2",
+                   "tiling_chosen": {k: sorted(set(v)) for k, v in tiles.items()}},
+        "e2e": None, "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 5), "peak_source": peak_kind, "traffic": None,
+                     "kernel": "whole epoch graph (algorithmic bytes of all positions / epoch time)"},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "grad_n1024_m256":
+        run_gpu_grad(args, world, rank, local)
+        return
+    if args.workload == "batch64":
+        run_gpu_batch(args, world, rank, local)
         return
     run_gpu(args, world, rank, local)
 

@@ -55,7 +55,8 @@ enum { EMG_SCATTER_DETERMINISTIC = 0, EMG_SCATTER_ATOMIC = 1 };
 /* Same object as cudaStream_t; NULL is the legacy default stream. */
 typedef struct CUstream_st* emg_stream_t;
 
-typedef struct emg_ctx emg_ctx; /* opaque, library-owned */
+typedef struct emg_ctx emg_ctx;     /* opaque, library-owned */
+typedef struct emg_batch emg_batch; /* opaque, library-owned */
 
 /*
  * The problem of Sec. 2.1: object size, probe size m, scan positions P_k
@@ -237,6 +238,36 @@ emg_status emg_simulate_intensity(const float* object, int32_t n_rows, int32_t n
  */
 emg_status emg_fft2(const float* in, float* out, int32_t m, int32_t count, int32_t inverse,
                     emg_stream_t stream);
+
+/*
+ * FFT tiling: the number of CTAs that share one scan position in the step
+ * kernel (1 for m <= 32; 2 or 4 for m = 64, 128; 8 for m = 256).  It changes
+ * speed only: results are identical for every valid choice.  EMG_ENOTSUP when
+ * the choice is not built or leaves a CTA without a row at the coarsest level.
+ */
+emg_status emg_set_cluster(emg_ctx* ctx, int32_t cluster);
+
+/*
+ * Autotuner: times a few minibatches (on private copies of the bound state,
+ * which is left untouched) for every valid FFT tiling and keeps the fastest.
+ * chosen (host, or NULL) receives it, ms_per_minibatch (host, or NULL) its
+ * time.  Synchronises.
+ */
+emg_status emg_autotune(emg_ctx* ctx, int32_t* chosen, double* ms_per_minibatch);
+
+/*
+ * Batches of independent reconstructions (problems of different object, probe
+ * and scan sizes).  emg_batch_create groups `count` contexts on one device,
+ * each with its state bound; the contexts stay owned by the caller and must
+ * outlive the batch.  emg_batch_run_epochs runs n_epochs epochs of every
+ * context with its default schedule (emg_schedule_permutation from its own
+ * seed and epoch counter), each epoch as ONE launch of a CUDA graph that holds
+ * one branch per context; results equal running each context alone.
+ * Asynchronous on `stream`.
+ */
+emg_status emg_batch_create(emg_batch** out, emg_ctx* const* ctxs, int32_t count);
+emg_status emg_batch_run_epochs(emg_batch* batch, int32_t n_epochs, emg_stream_t stream);
+void emg_batch_destroy(emg_batch* batch);
 
 /*
  * Kernel timing for measurement (not part of the method).  enable = 1 makes

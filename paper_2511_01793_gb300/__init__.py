@@ -27,6 +27,7 @@ __all__ = [
     "emg_step_minibatch", "emg_position_stats", "emg_set_verify", "emg_run_epochs", "emg_misfit",
     "emg_set_epoch", "emg_schedule_permutation", "emg_reconstruct_host",
     "emg_simulate_intensity", "emg_fft2", "emg_step_minibatch_noalloc", "emg_misfit_gradient",
+    "emg_set_cluster", "emg_autotune", "emg_batch_create", "emg_batch_run_epochs", "emg_batch_destroy",
     "emg_set_profiling",
     "emg_profile_read",
     "emg_last_error", "emg_destroy", "Context",
@@ -86,6 +87,11 @@ _SIGS = {
                                                   _VP, _VP, ctypes.c_int32, _I32P, ctypes.c_int32,
                                                   ctypes.POINTER(EmgParams), _VP]),
     "emg_misfit_gradient": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _F64P]),
+    "emg_set_cluster": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "emg_autotune": (ctypes.c_int, [_VP, _I32P, _F64P]),
+    "emg_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int32]),
+    "emg_batch_run_epochs": (ctypes.c_int, [_VP, ctypes.c_int32, _VP]),
+    "emg_batch_destroy": (None, [_VP]),
     "emg_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "emg_profile_read": (ctypes.c_int, [_VP, _F64P, ctypes.POINTER(ctypes.c_int64)]),
     "emg_last_error": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_char_p)]),
@@ -280,6 +286,34 @@ def emg_misfit_gradient(ctx: int, object_ptr: int, probe_ptr: int, grad_object_p
     return out.value if want_misfit else None
 
 
+def emg_set_cluster(ctx: int, cluster: int) -> None:
+    _check(load().emg_set_cluster(ctx, cluster), "emg_set_cluster", ctx)
+
+
+def emg_autotune(ctx: int):
+    """Returns (chosen cluster size, ms per minibatch)."""
+    c = ctypes.c_int32()
+    ms = ctypes.c_double()
+    _check(load().emg_autotune(ctx, ctypes.byref(c), ctypes.byref(ms)), "emg_autotune", ctx)
+    return c.value, ms.value
+
+
+def emg_batch_create(ctxs) -> int:
+    arr = (_VP * len(ctxs))(*ctxs)
+    out = _VP()
+    _check(load().emg_batch_create(ctypes.byref(out), arr, len(ctxs)), "emg_batch_create")
+    return out.value
+
+
+def emg_batch_run_epochs(batch: int, n_epochs: int, stream: int = 0) -> None:
+    _check(load().emg_batch_run_epochs(batch, n_epochs, _VP(stream)), "emg_batch_run_epochs")
+
+
+def emg_batch_destroy(batch: int) -> None:
+    if batch:
+        load().emg_batch_destroy(batch)
+
+
 def emg_set_profiling(ctx: int, enable: bool) -> None:
     _check(load().emg_set_profiling(ctx, int(bool(enable))), "emg_set_profiling", ctx)
 
@@ -323,8 +357,14 @@ class Context:
         if not torch.cuda.is_available():
             raise RuntimeError("the eMAGPIE library needs a CUDA device")
         dev = torch.device("cuda", torch.cuda.current_device())
-        self.pos = torch.as_tensor(np.ascontiguousarray(pos, dtype=np.int32)).to(dev)
-        self.intensity = torch.as_tensor(np.ascontiguousarray(intensity, dtype=np.float32)).to(dev)
+
+        def on_device(x, np_dtype, t_dtype):
+            if isinstance(x, torch.Tensor):
+                return x.to(device=dev, dtype=t_dtype).contiguous()
+            return torch.as_tensor(np.ascontiguousarray(x, dtype=np_dtype)).to(dev)
+
+        self.pos = on_device(pos, np.int32, torch.int32)
+        self.intensity = on_device(intensity, np.float32, torch.float32)
         n_pos, m = int(self.intensity.shape[0]), int(self.intensity.shape[-1])
         self.m, self.n_pos = m, n_pos
         self.stream = stream if stream is not None else torch.cuda.current_stream()

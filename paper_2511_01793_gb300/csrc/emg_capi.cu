@@ -26,6 +26,7 @@ struct emg_ctx {
   int n_rows = 0, n_cols = 0, m = 0, n_pos = 0;
   emg_params par{};
   int verify = 0;
+  int cluster = 1;                // CTAs per position in the step kernel (a tuning knob)
   int64_t epoch = 0;
   std::string err;
   int last_b = 0;
@@ -54,6 +55,7 @@ struct emg_ctx {
   float2* graph_object = nullptr;
   float2* graph_probe = nullptr;
   int graph_verify = -1;
+  int graph_cluster = -1;
   int64_t graph_counts[4] = {0, 0, 0, 0};
   float* d_wq = nullptr;          // [m][m]
   void* d_levels = nullptr;       // all multigrid arrays
@@ -76,6 +78,23 @@ struct emg_ctx {
   std::vector<int32_t> h_pos;
   PrepArgs prep{};
   emg::LevelArrays lv{};
+};
+
+// Several independent contexts whose epochs replay as one graph: one branch
+// per context, forked after a kernel that selects every context's order row
+// for the current epoch on the device.
+struct emg_batch {
+  std::vector<emg_ctx*> ctxs;
+  int device = 0;
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> forks;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<const void*> key;   // per context: d_orders, object, probe, cluster, verify
+  int32_t** d_src = nullptr;      // [count] device pointers to each context's order rows
+  int32_t** d_dst = nullptr;      // [count] each context's epoch order buffer
+  int* d_n = nullptr;             // [count] positions per context
+  int* d_epoch = nullptr;         // current epoch within the call
+  std::string err;
 };
 
 namespace {
@@ -162,7 +181,7 @@ emg_status validate_params(emg_ctx* c, const emg_params* p, int m, int n_pos) {
   if (p->scatter != EMG_SCATTER_DETERMINISTIC) return fail(c, EMG_EINVAL, "unknown scatter mode");
   if (p->joint != 0 && p->joint != 1) return fail(c, EMG_EINVAL, "joint must be 0 or 1");
   if (!(p->w_eps >= 0.f) || !isfinite(p->w_eps)) return fail(c, EMG_EINVAL, "w_eps must be finite and >= 0");
-  if (!emg::step_supported(m, p->levels))
+  if (!emg::step_supported(m, p->levels, emg::default_cluster(m)))
     return fail(c, EMG_ENOTSUP, "too many multigrid levels for this probe size");
   return EMG_OK;
 }
@@ -331,6 +350,7 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   sa.prolong = c->par.prolong;
   sa.joint = c->par.joint;
   sa.verify = c->verify;
+  sa.cluster = c->cluster;
   sa.alpha = c->par.alpha;
   sa.lv = c->lv;
   sa.zt = c->d_zt;
@@ -373,11 +393,24 @@ emg_status check_bound(emg_ctx* c) {
   return EMG_OK;
 }
 
+// Enqueues one epoch reading its order from d_epoch_order: the max|Q|^2 seed
+// and every minibatch (used inside graph capture).
+emg_status enqueue_epoch(emg_ctx* c, cudaStream_t s) {
+  emg_status st = seed_probe_max(c, s);
+  const int N = c->n_pos, B = c->par.minibatch;
+  int seq = 0;
+  for (int b0 = 0; st == EMG_OK && b0 < N; b0 += B) {
+    const int b = (N - b0 < B) ? N - b0 : B;
+    st = enqueue_minibatch(c, c->d_epoch_order + b0, b, c->d_phi + b0, seq++, s);
+  }
+  return st;
+}
+
 // Captures one epoch (probe-max seed + all minibatches reading d_epoch_order)
 // as a graph for the currently bound state; reused until the state changes.
 emg_status ensure_epoch_graph(emg_ctx* c) {
   if (c->graph && c->graph_object == c->object && c->graph_probe == c->probe &&
-      c->graph_verify == c->verify)
+      c->graph_verify == c->verify && c->graph_cluster == c->cluster)
     return EMG_OK;
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
@@ -386,13 +419,7 @@ emg_status ensure_epoch_graph(emg_ctx* c) {
   int64_t before[kKinds];
   for (int i = 0; i < kKinds; ++i) before[i] = c->launches[i];
   EMG_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  emg_status st = seed_probe_max(c, c->cap_stream);
-  const int N = c->n_pos, B = c->par.minibatch;
-  int seq = 0;
-  for (int b0 = 0; st == EMG_OK && b0 < N; b0 += B) {
-    const int b = (N - b0 < B) ? N - b0 : B;
-    st = enqueue_minibatch(c, c->d_epoch_order + b0, b, c->d_phi + b0, seq++, c->cap_stream);
-  }
+  emg_status st = enqueue_epoch(c, c->cap_stream);
   cudaGraph_t g = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
   for (int i = 0; i < kKinds; ++i) {
@@ -413,6 +440,7 @@ emg_status ensure_epoch_graph(emg_ctx* c) {
   c->graph_object = c->object;
   c->graph_probe = c->probe;
   c->graph_verify = c->verify;
+  c->graph_cluster = c->cluster;
   return EMG_OK;
 }
 
@@ -556,6 +584,7 @@ emg_status emg_create(emg_ctx** out, const emg_problem* pr, const emg_params* pa
   c->m = pr->m;
   c->n_pos = pr->n_pos;
   c->par = *par;
+  c->cluster = emg::default_cluster(pr->m);
   c->stream = (cudaStream_t)stream;
   auto bail = [&](emg_status s) {
     free_all(c);
@@ -810,6 +839,216 @@ emg_status emg_misfit_gradient(emg_ctx* c, const float* object, const float* pro
     *misfit = c->h_scalar[0];
   }
   return EMG_OK;
+}
+
+emg_status emg_set_cluster(emg_ctx* c, int32_t cluster) {
+  if (!c) return EMG_EINVAL;
+  if (!emg::step_supported(c->m, c->par.levels, cluster))
+    return fail(c, EMG_ENOTSUP, "cluster size not built or not valid for this probe size and level count");
+  c->cluster = cluster;
+  return EMG_OK;
+}
+
+emg_status emg_autotune(emg_ctx* c, int32_t* chosen, double* ms_per_minibatch) {
+  if (!c) return EMG_EINVAL;
+  emg_status st = check_bound(c);
+  if (st != EMG_OK) return st;
+  DeviceGuard g(c->device);
+  const int cands[] = {1, 2, 4, 8};
+  const size_t nz = (size_t)c->n_rows * c->n_cols, nq = (size_t)c->m * c->m;
+  float2 *tz = nullptr, *tq = nullptr;
+  if (cudaMalloc(&tz, nz * sizeof(float2)) != cudaSuccess || cudaMalloc(&tq, nq * sizeof(float2)) != cudaSuccess) {
+    cudaFree(tz);
+    return fail(c, EMG_ENOMEM, "autotune scratch");
+  }
+  float2* keep_o = c->object;
+  float2* keep_p = c->probe;
+  const int keep_cluster = c->cluster, keep_profile = c->profile;
+  int best = keep_cluster;
+  double best_ms = 1e30;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int B = c->par.minibatch;
+  std::vector<int32_t> idx(B);
+  for (int i = 0; i < B; ++i) idx[i] = (int32_t)(((int64_t)i * 7919) % c->n_pos);
+  for (int cand : cands) {
+    if (!emg::step_supported(c->m, c->par.levels, cand)) continue;
+    c->cluster = cand;
+    c->profile = 0;
+    cudaMemcpyAsync(tz, keep_o, nz * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tq, keep_p, nq * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream);
+    c->object = tz;
+    c->probe = tq;
+    if ((st = ensure_orders(c, (size_t)c->n_pos)) != EMG_OK) break;
+    cudaMemcpyAsync(c->d_orders, idx.data(), B * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+    for (int r = 0; r < 2 && st == EMG_OK; ++r) st = enqueue_minibatch(c, c->d_orders, B, c->d_phi, r, c->stream);
+    cudaEventRecord(e0, c->stream);
+    const int reps = 6;
+    for (int r = 0; r < reps && st == EMG_OK; ++r) {
+      if (r % 2 == 0) st = seed_probe_max(c, c->stream);
+      if (st == EMG_OK) st = enqueue_minibatch(c, c->d_orders, B, c->d_phi, r, c->stream);
+    }
+    cudaEventRecord(e1, c->stream);
+    if (st != EMG_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      st = cuda_fail(c, cudaGetLastError(), "autotune");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms / reps < best_ms) {
+      best_ms = ms / reps;
+      best = cand;
+    }
+  }
+  cudaStreamSynchronize(c->stream);
+  c->object = keep_o;
+  c->probe = keep_p;
+  c->profile = keep_profile;
+  c->cluster = best;
+  for (int i = 0; i < kKinds; ++i) c->launches[i] = 0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(tz);
+  cudaFree(tq);
+  if (st != EMG_OK) return st;
+  if (chosen) *chosen = best;
+  if (ms_per_minibatch) *ms_per_minibatch = best_ms;
+  return EMG_OK;
+}
+
+emg_status emg_batch_create(emg_batch** out, emg_ctx* const* ctxs, int32_t count) {
+  if (!out) return EMG_EINVAL;
+  *out = nullptr;
+  if (!ctxs || count < 1) return EMG_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!ctxs[i] || ctxs[i]->device != ctxs[0]->device || !ctxs[i]->object || !ctxs[i]->probe) return EMG_EINVAL;
+  emg_batch* b = new (std::nothrow) emg_batch();
+  if (!b) return EMG_ENOMEM;
+  b->ctxs.assign(ctxs, ctxs + count);
+  b->device = ctxs[0]->device;
+  DeviceGuard g(b->device);
+  bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaMalloc(&b->d_src, count * sizeof(int32_t*)) == cudaSuccess &&
+            cudaMalloc(&b->d_dst, count * sizeof(int32_t*)) == cudaSuccess &&
+            cudaMalloc(&b->d_n, count * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&b->d_epoch, sizeof(int)) == cudaSuccess;
+  for (int i = 0; ok && i < count; ++i) {
+    cudaStream_t f;
+    ok = cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) b->forks.push_back(f);
+  }
+  if (!ok) {
+    emg_batch_destroy(b);
+    return EMG_ENOMEM;
+  }
+  *out = b;
+  return EMG_OK;
+}
+
+emg_status emg_batch_run_epochs(emg_batch* b, int32_t n_epochs, emg_stream_t stream) {
+  if (!b || n_epochs < 0) return EMG_EINVAL;
+  if (n_epochs == 0) return EMG_OK;
+  DeviceGuard g(b->device);
+  const int K = (int)b->ctxs.size();
+  const cudaStream_t s = (cudaStream_t)stream;
+  // every context's orders for this call (its default schedule), uploaded once
+  std::vector<int32_t*> src(K), dst(K);
+  std::vector<int> ns(K);
+  std::vector<const void*> key;
+  for (int i = 0; i < K; ++i) {
+    emg_ctx* c = b->ctxs[i];
+    const int N = c->n_pos;
+    std::vector<int32_t> h((size_t)n_epochs * N);
+    for (int32_t e = 0; e < n_epochs; ++e) permutation(c->par.seed, c->epoch + e, N, h.data() + (size_t)e * N);
+    emg_status st = ensure_orders(c, h.size());
+    if (st != EMG_OK) return st;
+    if (cudaMemcpyAsync(c->d_orders, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return EMG_ECUDA;
+    src[i] = c->d_orders;
+    dst[i] = c->d_epoch_order;
+    ns[i] = N;
+    key.insert(key.end(), {c->d_orders, c->object, c->probe, (const void*)(intptr_t)c->cluster,
+                           (const void*)(intptr_t)c->verify, (const void*)(intptr_t)c->profile});
+  }
+  if (cudaMemcpyAsync(b->d_src, src.data(), K * sizeof(int32_t*), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_dst, dst.data(), K * sizeof(int32_t*), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_n, ns.data(), K * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(b->d_epoch, 0, sizeof(int), s) != cudaSuccess)
+    return EMG_ECUDA;
+  if (!b->graph || key != b->key) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return EMG_ECUDA;
+    cudaError_t ce = emg::launch_batch_orders(b->d_src, b->d_dst, b->d_n, K, b->d_epoch, b->cap);
+    cudaEvent_t fork_ev, join_ev;
+    cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming);
+    cudaEventRecord(fork_ev, b->cap);
+    emg_status st = ce == cudaSuccess ? EMG_OK : EMG_ECUDA;
+    std::vector<cudaEvent_t> joins;
+    for (int i = 0; i < K && st == EMG_OK; ++i) {
+      cudaStreamWaitEvent(b->forks[i], fork_ev, 0);
+      emg_ctx* c = b->ctxs[i];
+      const int keep_profile = c->profile;
+      c->profile = 0;
+      int64_t before[kKinds];
+      for (int k2 = 0; k2 < kKinds; ++k2) before[k2] = c->launches[k2];
+      st = enqueue_epoch(c, b->forks[i]);
+      for (int k2 = 0; k2 < kKinds; ++k2) {
+        c->graph_counts[k2] = c->launches[k2] - before[k2];
+        c->launches[k2] = before[k2];
+      }
+      c->profile = keep_profile;
+      cudaEvent_t j;
+      cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+      cudaEventRecord(j, b->forks[i]);
+      cudaStreamWaitEvent(b->cap, j, 0);
+      joins.push_back(j);
+    }
+    if (st == EMG_OK) ce = emg::launch_epoch_advance(b->d_epoch, b->cap);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->cap, &gr);
+    cudaEventDestroy(fork_ev);
+    cudaEventDestroy(join_ev);
+    for (cudaEvent_t j : joins) cudaEventDestroy(j);
+    if (st != EMG_OK || ce != cudaSuccess || ee != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      return st != EMG_OK ? st : EMG_ECUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&b->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (ie != cudaSuccess) {
+      b->graph = nullptr;
+      return EMG_ECUDA;
+    }
+    b->key = key;
+  }
+  for (int32_t e = 0; e < n_epochs; ++e) {
+    if (cudaGraphLaunch(b->graph, s) != cudaSuccess) return EMG_ECUDA;
+    for (emg_ctx* c : b->ctxs)
+      for (int k2 = 0; k2 < kKinds; ++k2) c->launches[k2] += c->graph_counts[k2];
+  }
+  for (emg_ctx* c : b->ctxs) c->epoch += n_epochs;
+  return cudaGetLastError() == cudaSuccess ? EMG_OK : EMG_ECUDA;
+}
+
+void emg_batch_destroy(emg_batch* b) {
+  if (!b) return;
+  {
+    DeviceGuard g(b->device);
+    if (b->cap) cudaStreamSynchronize(b->cap);
+    cudaDeviceSynchronize();
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaStream_t f : b->forks) cudaStreamDestroy(f);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->d_src);
+    cudaFree(b->d_dst);
+    cudaFree(b->d_n);
+    cudaFree(b->d_epoch);
+  }
+  delete b;
 }
 
 emg_status emg_set_profiling(emg_ctx* c, int32_t enable) {

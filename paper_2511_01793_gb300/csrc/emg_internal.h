@@ -49,6 +49,7 @@ struct StepArgs {
   const unsigned* mq;           // max|Q|^2 of the probe (float bits), read by the cluster step
   int n_rows, n_cols;
   int levels, prolong, joint, verify;
+  int cluster;                  // CTAs per position: 1 (m <= 32 only), 2, 4 or 8 (m = 256)
   float alpha;                  // rPIE constant (level-0 gain formed in the cluster step)
   LevelArrays lv;
   float2* zt;                   // [b][m*m] joint-step object patches z~_k
@@ -112,7 +113,12 @@ struct GradReduceArgs {
 
 cudaError_t launch_gradient(int m, int b, const GradArgs& a, cudaStream_t s);
 cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t s);
-bool step_supported(int m, int levels);
+bool step_supported(int m, int levels, int cluster);
+int default_cluster(int m);
+// Copies, for each of `count` problems, its order row `*epoch` into its epoch buffer.
+cudaError_t launch_batch_orders(const int32_t* const* src, int32_t* const* dst, const int* n, int count,
+                                const int* epoch, cudaStream_t s);
+cudaError_t launch_epoch_advance(int* epoch, cudaStream_t s);
 
 constexpr int kApplyTile = 16;
 constexpr int kApplyThreads = 256;      // one object pixel per thread

@@ -1621,15 +1621,6 @@ cudaError_t upload_twiddles() {
   if ((e = set_step_smem<32>()) != cudaSuccess) return e;
   if ((e = set_step_smem<64>()) != cudaSuccess) return e;
   if ((e = set_step_smem<128>()) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_stepc<64, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(CTile<64, 2>::smem_elems * sizeof(float2)))) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_stepc<128, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(CTile<128, 2>::smem_elems * sizeof(float2)))) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_stepc<256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(CTile<256, 8>::smem_elems * sizeof(float2)))) != cudaSuccess)
-    return e;
   if ((e = set_cluster_attrs()) != cudaSuccess) return e;
   if ((e = set_aux_smem<16>()) != cudaSuccess) return e;
   if ((e = set_aux_smem<32>()) != cudaSuccess) return e;
@@ -1766,6 +1757,19 @@ cudaError_t set_grad_attrs() {
 // Dynamic shared-memory limits of the cluster kernels (once per device).
 cudaError_t set_cluster_attrs() {
   cudaError_t e;
+  if ((e = set_cluster_smem(k_stepc<16, 2>, CTile<16, 2>::smem_elems)) != cudaSuccess) return e;
+  if ((e = set_cluster_smem(k_stepc<32, 2>, CTile<32, 2>::smem_elems)) != cudaSuccess) return e;
+  if ((e = set_cluster_smem(k_stepc<64, 4>, CTile<64, 4>::smem_elems)) != cudaSuccess) return e;
+  if ((e = set_cluster_smem(k_stepc<128, 4>, CTile<128, 4>::smem_elems)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_stepc<64, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(CTile<64, 2>::smem_elems * sizeof(float2)))) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_stepc<128, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(CTile<128, 2>::smem_elems * sizeof(float2)))) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_stepc<256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(CTile<256, 8>::smem_elems * sizeof(float2)))) != cudaSuccess)
+    return e;
   if ((e = set_cluster_smem(k_fwdc<256, 8, 0>, CTile<256, 8>::smem_elems)) != cudaSuccess) return e;
   if ((e = set_cluster_smem(k_fwdc<256, 8, 1>, CTile<256, 8>::smem_elems)) != cudaSuccess) return e;
   if ((e = set_cluster_smem(k_fwdc<256, 8, 2>, CTile<256, 8>::smem_elems)) != cudaSuccess) return e;
@@ -1781,9 +1785,8 @@ cudaError_t set_cluster_attrs() {
   return cudaSuccess;
 }
 
-template <int M>
+template <int M, int C>
 cudaError_t launch_stepc_t(int b, const StepArgs& a, cudaStream_t s) {
-  constexpr int C = ClusterSize<M>::value;
   using TL = CTile<M, C>;
   cudaError_t e = launch_cluster_pdl(k_stepc<M, C>, C, dim3(C * b), dim3(TL::NT), TL::smem_elems * sizeof(float2),
                                      s, a);
@@ -1792,10 +1795,43 @@ cudaError_t launch_stepc_t(int b, const StepArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_step(int m, int b, const StepArgs& a, cudaStream_t s) {
-  if (m == 256) return launch_stepc_t<256>(b, a, s);
-  if (m == 128) return launch_stepc_t<128>(b, a, s);
-  if (m == 64) return launch_stepc_t<64>(b, a, s);
-  EMG_DISPATCH_M(m, (launch_step_t<M>(b, a, s)));
+  switch (m * 16 + a.cluster) {
+    case 16 * 16 + 1: return launch_step_t<16>(b, a, s);
+    case 16 * 16 + 2: return launch_stepc_t<16, 2>(b, a, s);
+    case 32 * 16 + 1: return launch_step_t<32>(b, a, s);
+    case 32 * 16 + 2: return launch_stepc_t<32, 2>(b, a, s);
+    case 64 * 16 + 2: return launch_stepc_t<64, 2>(b, a, s);
+    case 64 * 16 + 4: return launch_stepc_t<64, 4>(b, a, s);
+    case 128 * 16 + 2: return launch_stepc_t<128, 2>(b, a, s);
+    case 128 * 16 + 4: return launch_stepc_t<128, 4>(b, a, s);
+    case 256 * 16 + 8: return launch_stepc_t<256, 8>(b, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int default_cluster(int m) { return m <= 32 ? 1 : (m == 256 ? 8 : 2); }
+
+// Copies, per problem, the order row of the current epoch into the buffer its
+// captured minibatch kernels read.  One block per problem.
+__global__ void __launch_bounds__(256) k_batch_orders(const int32_t* const* src, int32_t* const* dst, const int* n,
+                                                      const int* epoch) {
+  const int q = blockIdx.x;
+  const int len = n[q];
+  const int32_t* from = src[q] + (size_t)(*epoch) * len;
+  for (int i = threadIdx.x; i < len; i += 256) dst[q][i] = from[i];
+}
+
+__global__ void k_epoch_advance(int* epoch) { *epoch += 1; }
+
+cudaError_t launch_batch_orders(const int32_t* const* src, int32_t* const* dst, const int* n, int count,
+                                const int* epoch, cudaStream_t s) {
+  k_batch_orders<<<count, 256, 0, s>>>(src, dst, n, epoch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_epoch_advance(int* epoch, cudaStream_t s) {
+  k_epoch_advance<<<1, 1, 0, s>>>(epoch);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
@@ -1873,17 +1909,20 @@ cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Whether the step kernel for probe side m supports `levels` multigrid levels.
-bool step_supported(int m, int levels) {
-  if (m <= 32) return step_smem_bytes(m, levels) <= (size_t)step_smem_limit();
-  const int C = (m == 256) ? 8 : 2;
-  if ((m >> (levels - 1)) < C) return false;  // every CTA needs a row at the coarsest level
+// Whether the step kernel for probe side m with `cluster` CTAs per position
+// supports `levels` multigrid levels.
+bool step_supported(int m, int levels, int cluster) {
+  const bool built = (cluster == 1 && m <= 32) || (cluster == 2 && m <= 128) || (cluster == 4 && (m == 64 || m == 128)) ||
+                     (cluster == 8 && m == 256);
+  if (!built) return false;
+  if (cluster == 1) return step_smem_bytes(m, levels) <= (size_t)step_smem_limit();
+  if ((m >> (levels - 1)) < cluster) return false;  // every CTA needs a row at the coarsest level
   size_t need = 0;
   for (int l = 1; l < levels; ++l) {
-    const size_t wl = (size_t)m >> l, hl = wl / C;
+    const size_t wl = (size_t)m >> l, hl = wl / cluster;
     need += (2 * hl + 2) * (wl + 1);
   }
-  return need <= (size_t)m * (m / C + 1);
+  return need <= (size_t)m * (m / cluster + 1);
 }
 
 cudaError_t launch_normalize_probe(const float* amp, int m, int n_pos, float2* probe,
