@@ -240,6 +240,22 @@ emg_status emg_fft2(const float* in, float* out, int32_t m, int32_t count, int32
                     emg_stream_t stream);
 
 /*
+ * The same batched 2-D DFT on the tensor cores (the precision variant of the
+ * FFT pair of Sec. 2.1): each 1-D pass is a GEMM of the rows of all tiles with
+ * the 2m x 2m real matrix of x -> x F (or x conj(F)) in BF16, every operand
+ * split into high and low parts (x = xh + xl, xh = bf16(x), xl = bf16(x - xh))
+ * and the products xh yh + xh yl + xl yh accumulated in FP32.  The relative
+ * error per transform is of order 3 u^2 per pass, u = 2^-8 (about 1e-4 in the
+ * L2 norm), against about 1e-7 for emg_fft2.
+ *  in, out  device complex64 [count][m][m], natural order; may not alias
+ *  m        128 or 256 (EMG_ENOTSUP otherwise)
+ * Allocates and frees its split buffers and synchronises the stream.
+ * EMG_ETIMEOUT when a bounded wait inside the kernel gave up.
+ */
+emg_status emg_dft2_bf16x3(const float* in, float* out, int32_t m, int32_t count, int32_t inverse,
+                           emg_stream_t stream);
+
+/*
  * FFT tiling: the number of CTAs that share one scan position in the step
  * kernel (1 for m <= 32; 2 or 4 for m = 64, 128; 8 for m = 256).  It changes
  * speed only: results are identical for every valid choice.  EMG_ENOTSUP when

@@ -26,7 +26,7 @@ __all__ = [
     "emg_create", "emg_set_intensity", "emg_bind_state", "emg_normalize_probe",
     "emg_step_minibatch", "emg_position_stats", "emg_set_verify", "emg_run_epochs", "emg_misfit",
     "emg_set_epoch", "emg_schedule_permutation", "emg_reconstruct_host",
-    "emg_simulate_intensity", "emg_fft2", "emg_step_minibatch_noalloc", "emg_misfit_gradient",
+    "emg_simulate_intensity", "emg_fft2", "emg_dft2_bf16x3", "emg_step_minibatch_noalloc", "emg_misfit_gradient",
     "emg_set_cluster", "emg_autotune", "emg_batch_create", "emg_batch_run_epochs", "emg_batch_destroy",
     "emg_set_profiling",
     "emg_profile_read",
@@ -83,6 +83,7 @@ _SIGS = {
     "emg_simulate_intensity": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_int32,
                                               _VP, ctypes.c_int32, _VP, _VP]),
     "emg_fft2": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP]),
+    "emg_dft2_bf16x3": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP]),
     "emg_step_minibatch_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_int32,
                                                   _VP, _VP, ctypes.c_int32, _I32P, ctypes.c_int32,
                                                   ctypes.POINTER(EmgParams), _VP]),
@@ -262,6 +263,11 @@ def emg_simulate_intensity(object_ptr: int, n_rows: int, n_cols: int, probe_ptr:
 
 def emg_fft2(in_ptr: int, out_ptr: int, m: int, count: int, inverse: bool, stream: int = 0) -> None:
     _check(load().emg_fft2(in_ptr, out_ptr, m, count, int(bool(inverse)), _VP(stream)), "emg_fft2")
+
+
+def emg_dft2_bf16x3(in_ptr: int, out_ptr: int, m: int, count: int, inverse: bool, stream: int = 0) -> None:
+    _check(load().emg_dft2_bf16x3(in_ptr, out_ptr, m, count, int(bool(inverse)), _VP(stream)),
+           "emg_dft2_bf16x3")
 
 
 def emg_step_minibatch_noalloc(object_ptr: int, n_rows: int, n_cols: int, probe_ptr: int, m: int,

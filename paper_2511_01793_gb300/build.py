@@ -1,6 +1,6 @@
 """Builds the sm_103a shared library ``_lib/libemagpie.so`` in-tree with nvcc.
 
-The two translation units compile in parallel; the link step produces one
+The translation units compile in parallel; the link step produces one
 shared object exporting the C ABI of ``include/emagpie.h``.  The build is
 skipped when the sources and flags are unchanged since the last build.
 """
@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB_NAME = "libemagpie.so"
-SOURCES = ["emg_kernels.cu", "emg_capi.cu"]
+SOURCES = ["emg_kernels.cu", "emg_capi.cu", "emg_tc.cu"]
 HEADERS = ["emg_fft.cuh", "emg_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ftz=true: FP32 denormals flush to zero (the data never come near 1e-38).

@@ -789,6 +789,25 @@ emg_status emg_fft2(const float* in, float* out, int32_t m, int32_t count, int32
   return e == cudaSuccess ? EMG_OK : EMG_ECUDA;
 }
 
+emg_status emg_dft2_bf16x3(const float* in, float* out, int32_t m, int32_t count, int32_t inverse,
+                           emg_stream_t stream) {
+  if (!in || !out || in == out || count < 0 || (inverse != 0 && inverse != 1)) return EMG_EINVAL;
+  if (!emg::tc_supported(m)) return EMG_ENOTSUP;
+  if (count == 0) return EMG_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || ensure_device_init(dev) != cudaSuccess) return EMG_ECUDA;
+  const cudaStream_t s = (cudaStream_t)stream;
+  emg::TcWork* w = nullptr;
+  if (emg::tc_work_create(&w, m, count) != cudaSuccess) return EMG_ENOMEM;
+  cudaError_t e = emg::tc_dft2(w, (const float2*)in, (float2*)out, count, inverse, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int flag = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, emg::tc_error_flag(w), sizeof(int), cudaMemcpyDeviceToHost);
+  emg::tc_work_destroy(w);
+  if (e != cudaSuccess) return EMG_ECUDA;
+  return flag ? EMG_ETIMEOUT : EMG_OK;
+}
+
 emg_status emg_misfit_gradient(emg_ctx* c, const float* object, const float* probe, float* grad_object,
                                float* grad_probe, double* misfit) {
   if (!c) return EMG_EINVAL;

@@ -95,6 +95,11 @@ def test_context_free_calls_validate_arguments(lib):
     assert lib.emg_fft2(0x10, 0x10, 32, 1, 2, None) == emg.EMG_EINVAL
     assert lib.emg_simulate_intensity(None, 8, 8, None, 32, None, 1, None, None) == emg.EMG_EINVAL
     assert lib.emg_schedule_permutation(1, -1, 4, None) == emg.EMG_EINVAL
+    assert lib.emg_dft2_bf16x3(None, 0x10, 128, 1, 0, None) == emg.EMG_EINVAL
+    assert lib.emg_dft2_bf16x3(0x10, 0x10, 128, 1, 0, None) == emg.EMG_EINVAL   # aliasing
+    assert lib.emg_dft2_bf16x3(0x10, 0x20, 128, 1, 2, None) == emg.EMG_EINVAL
+    assert lib.emg_dft2_bf16x3(0x10, 0x20, 64, 1, 0, None) == emg.EMG_ENOTSUP
+    assert lib.emg_dft2_bf16x3(0x10, 0x20, 256, 0, 0, None) == emg.EMG_OK      # empty batch
     lib.emg_destroy(None)  # no-op
 
 
