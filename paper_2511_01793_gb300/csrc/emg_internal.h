@@ -57,6 +57,10 @@ struct StepArgs {
   float* mu;                    // [b] max |z_k|^2
   double* phi;                  // [b] Phi_k at the snapshot
   double* phi_after;            // [b] Phi~_k(Q~, z~_k) (verify only)
+  // tensor-core DFT path: R_k from outside and the misfit partial sums of each position
+  const float2* r_in;           // [b][m][m] natural order, or null (FFT path)
+  const double* r_partial;      // [b][r_tiles] sums of (|Psi| - a)^2
+  int r_tiles;
 };
 
 struct ApplyArgs {
@@ -131,6 +135,8 @@ cudaError_t launch_probe_max(const float2* probe, int m, unsigned* slot, cudaStr
 // Fills tile/halo of a and returns true when the tiled prep fits in shared memory.
 bool prep_tiled_config(PrepArgs& a);
 cudaError_t launch_step(int m, int b, const StepArgs& a, cudaStream_t s);
+// The step with R_k and the misfit partials given (a.r_in, a.r_partial): m = 128 (cluster 2, 4), 256 (8).
+cudaError_t launch_step_rin(int m, int b, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
 cudaError_t launch_misfit(int m, const float2* object, const float2* probe, const int32_t* pos,
                           const float* amp, int n_rows, int n_cols, int n_pos, double* partial,
@@ -143,6 +149,31 @@ cudaError_t launch_fft2(int m, const float2* in, float2* out, int count, int inv
 cudaError_t launch_normalize_probe(const float* amp, int m, int n_pos, float2* probe,
                                    double* scratch, int scratch_len, cudaStream_t s);
 size_t step_smem_bytes(int m, int levels);
+
+// Tensor-core DFT pair (BF16 split into three products, FP32 accumulation) for
+// m = 128 and 256; see emg_tc.cu.  A TcWork holds the split operand buffers of
+// up to `cap` tiles and their TMA descriptors.
+struct TcWork;
+struct TcStepArgs {
+  const float2* object;
+  const float2* probe;
+  const int32_t* pos;
+  const int32_t* order;         // [b] positions of the minibatch
+  int n_rows, n_cols, b;
+  const float* amp_t;           // [N][m][m] a_k transposed
+  float2* R;                    // [b][m][m] out: revised exit waves, natural order
+  double* partial;              // [b][tc_tiles_per_position(m)] out: sums of (|Psi| - a)^2
+};
+bool tc_supported(int m);
+cudaError_t tc_work_create(TcWork** out, int m, int cap);
+void tc_work_destroy(TcWork* w);
+int* tc_error_flag(TcWork* w);
+int tc_tiles_per_position(int m);
+// count tiles of m x m complex64: out = F x (inverse = 0) or F^-1 x (inverse = 1).
+cudaError_t tc_dft2(TcWork* w, const float2* in, float2* out, int count, int inverse, cudaStream_t s);
+// a1-a4 of a minibatch: psi_k, Psi_k, modulus replacement, R_k.
+cudaError_t tc_exit_waves(TcWork* w, const TcStepArgs& a, cudaStream_t s);
+cudaError_t launch_tc_amp(const float* d, float* amp_t, int m, int n_pos, cudaStream_t s);
 int step_smem_limit();
 
 }  // namespace emg

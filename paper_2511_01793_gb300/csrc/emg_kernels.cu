@@ -674,7 +674,10 @@ __device__ __forceinline__ T prolong_halo(const T* y, int sl, int wc, int lr, in
   return lerp4<T>(v, y[i2 * sl + j], y[i * sl + j2], y[i2 * sl + j2]);
 }
 
-template <int M, int C>
+// RIN = true: the revised exit waves R_k and the misfit partials come from the
+// tensor-core DFT pair (a2-a4 done elsewhere); the kernel gathers z_k and runs
+// a5-a7 only.
+template <int M, int C, bool RIN = false>
 __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) {
   using TL = CTile<M, C>;
   constexpr int NT = TL::NT, H = TL::H, SR = TL::SR, SC = TL::SC;
@@ -696,13 +699,15 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
   const int row0 = rank * H;
 
   // amplitudes of my spectral slots: issued now, consumed after the row passes
-  const float* amp = a.amp + (size_t)k * M * M + rank * H;
   float am_reg[SLOTS][N1];
+  if constexpr (!RIN) {
+    const float* amp = a.amp + (size_t)k * M * M + rank * H;
 #pragma unroll
-  for (int t = 0; t < SLOTS; ++t) {
-    const int s = tid + t * NT, k2 = s / H, lc = s % H;
+    for (int t = 0; t < SLOTS; ++t) {
+      const int s = tid + t * NT, k2 = s / H, lc = s % H;
 #pragma unroll
-    for (int i = 0; i < N1; ++i) am_reg[t][i] = __ldg(amp + (i + N1 * k2) * M + lc);
+      for (int i = 0; i < N1; ++i) am_reg[t][i] = __ldg(amp + (i + N1 * k2) * M + lc);
+    }
   }
   pdl_trigger();
   pdl_wait();  // object, probe, max|Q|^2 and level arrays come from earlier kernels
@@ -717,24 +722,30 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
     const int lr = p / M, c = p % M, r = row0 + lr;
     const float2 zk = gather_obj(a.object, a.n_rows, a.n_cols, o_r + r, o_c + c);
     zbuf[p] = zk;
-    rowbuf[lr * SR + c] = cmul(a.probe[r * M + c], zk);
+    if constexpr (RIN)
+      rowbuf[lr * SR + c] = a.r_in[(size_t)kb * M * M + r * M + c];
+    else
+      rowbuf[lr * SR + c] = cmul(a.probe[r * M + c], zk);
     mu_l = fmaxf(mu_l, cabs2(zk));
   }
   const float mu_part = block_max<NT>(mu_l, redf);
-  // a2: row passes on my rows
-  gpass_a_fwd<M, H, SR, 1, NT>(rowbuf, tid);
-  __syncthreads();
-  gpass_b<M, H, SR, 1, NT, false>(rowbuf, tid);
-  __syncthreads();
+  if constexpr (!RIN) {
+    // a2: row passes on my rows
+    gpass_a_fwd<M, H, SR, 1, NT>(rowbuf, tid);
+    __syncthreads();
+    gpass_b<M, H, SR, 1, NT, false>(rowbuf, tid);
+    __syncthreads();
+  }
   cl.barrier_wait();  // all CTAs of the cluster resident
   // transpose 1: my rows x all storage columns -> column slabs
-  cluster_rows_to_cols<M, C>(cl, rank, rowbuf, colbuf, tid);
+  if constexpr (!RIN) cluster_rows_to_cols<M, C>(cl, rank, rowbuf, colbuf, tid);
   if (tid == 0) cluster_publish<C>(cl, rank, xf, mu_part);
   cl.sync();
   float mu = xf[0];
 #pragma unroll
   for (int d = 1; d < C; ++d) mu = fmaxf(mu, xf[d]);
 
+  if constexpr (!RIN) {
   // a2 (columns) + a3 + a4 (columns) on my storage columns
   gpass_a_fwd<M, H, 1, SC, NT>(colbuf, tid);
   __syncthreads();
@@ -777,6 +788,7 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
   __syncthreads();
   gpass_a_inv<M, H, SR, 1, NT>(rowbuf, tid);
   __syncthreads();
+  }  // !RIN
 
   // a5: MAGPIE multigrid on row slabs; level-l buffers (l >= 1) reuse colbuf.
   // Z_l keeps one halo row above and below my rows for the prolongation.
@@ -940,9 +952,11 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
     double phi = 0.0, after = 0.0;
 #pragma unroll
     for (int d = 0; d < C; ++d) {
-      phi += xd[d];
+      if constexpr (!RIN) phi += xd[d];
       after += xd2[d];
     }
+    if constexpr (RIN)
+      for (int t = 0; t < a.r_tiles; ++t) phi += a.r_partial[(size_t)kb * a.r_tiles + t];
     a.mu[kb] = mu;
     a.phi[kb] = phi * (0.5 / (double)(M * M));
     if (a.verify) a.phi_after[kb] = after;
@@ -1770,6 +1784,9 @@ cudaError_t set_cluster_attrs() {
   if ((e = cudaFuncSetAttribute(k_stepc<256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(CTile<256, 8>::smem_elems * sizeof(float2)))) != cudaSuccess)
     return e;
+  if ((e = set_cluster_smem(k_stepc<128, 2, true>, CTile<128, 2>::smem_elems)) != cudaSuccess) return e;
+  if ((e = set_cluster_smem(k_stepc<128, 4, true>, CTile<128, 4>::smem_elems)) != cudaSuccess) return e;
+  if ((e = set_cluster_smem(k_stepc<256, 8, true>, CTile<256, 8>::smem_elems)) != cudaSuccess) return e;
   if ((e = set_cluster_smem(k_fwdc<256, 8, 0>, CTile<256, 8>::smem_elems)) != cudaSuccess) return e;
   if ((e = set_cluster_smem(k_fwdc<256, 8, 1>, CTile<256, 8>::smem_elems)) != cudaSuccess) return e;
   if ((e = set_cluster_smem(k_fwdc<256, 8, 2>, CTile<256, 8>::smem_elems)) != cudaSuccess) return e;
@@ -1792,6 +1809,24 @@ cudaError_t launch_stepc_t(int b, const StepArgs& a, cudaStream_t s) {
                                      s, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+template <int M, int C>
+cudaError_t launch_stepc_rin_t(int b, const StepArgs& a, cudaStream_t s) {
+  using TL = CTile<M, C>;
+  cudaError_t e = launch_cluster_pdl(k_stepc<M, C, true>, C, dim3(C * b), dim3(TL::NT),
+                                     TL::smem_elems * sizeof(float2), s, a);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_rin(int m, int b, const StepArgs& a, cudaStream_t s) {
+  switch (m * 16 + a.cluster) {
+    case 128 * 16 + 2: return launch_stepc_rin_t<128, 2>(b, a, s);
+    case 128 * 16 + 4: return launch_stepc_rin_t<128, 4>(b, a, s);
+    case 256 * 16 + 8: return launch_stepc_rin_t<256, 8>(b, a, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_step(int m, int b, const StepArgs& a, cudaStream_t s) {
