@@ -53,10 +53,11 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "grad_n1024_m256", "batch64"],
+                    choices=[WORKLOAD, "grad_n1024_m256", "batch64", "prec_n2048_m256"],
                     help="mg_n512_m128: eMAGPIE epochs (default); grad_n1024_m256: exit-wave "
                          "misfit gradient over all positions; batch64: 64 uneven reconstructions, "
-                         "one graph launch per epoch")
+                         "one graph launch per epoch; prec_n2048_m256: epochs with the DFT pair on "
+                         "tensor cores (BF16 split) against FP32 FFTs, and time to the oracle's misfit")
     return ap.parse_args()
 
 
@@ -499,6 +500,151 @@ def run_gpu_grad(args, world, rank, local):
     ctx.close()
 
 
+PREC_WORKLOAD = "prec_n2048_m256"
+PREC_TARGET = os.path.join(ROOT, "tests", "golden", f"{PREC_WORKLOAD}_oracle_misfit.txt")
+
+
+def read_prec_target():
+    """(epochs, Phi) of the FP64 oracle's last stored epoch, or (None, None)."""
+    if not os.path.exists(PREC_TARGET):
+        return None, None
+    rows = [ln.split() for ln in open(PREC_TARGET) if ln.strip() and not ln.startswith("#")]
+    return int(rows[-1][0]), float(rows[-1][1])
+
+
+def run_gpu_prec(args, world, rank, local):
+    """The precision workload: the same eMAGPIE epochs with the DFT pair as FP32
+    shared-memory FFTs and as BF16-split GEMMs on the tensor cores; throughput
+    of both and wall time until each reaches the FP64 oracle's misfit."""
+    import torch
+
+    import paper_2511_01793_gb300 as emg
+
+    torch.cuda.set_device(local)
+    emg.build()
+    emg.load()
+    w = synth.make_workload(PREC_WORKLOAD)
+    p = w.params
+    n, m, N, B = p["n"], p["m"], len(w.pos), p["minibatch"]
+    d = host_intensities(w, rank)
+    e_target, phi_target = read_prec_target()
+    max_epochs = 3 * e_target if e_target else 0
+    orders = synth.epoch_orders(N, max(max_epochs, args.warmup + args.steps + 2), p["order_seed"])
+    stream = torch.cuda.Stream()
+    res = {}
+    with torch.cuda.stream(stream):
+        d_dev = torch.from_numpy(d).cuda()
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        for name, dft in (("fft32", emg.EMG_DFT_FFT32), ("bf16x3", emg.EMG_DFT_BF16X3)):
+            params = emg.emg_default_params(alpha=p["alpha"], levels=p["levels"], minibatch=B,
+                                            prolong=emg.EMG_PROLONG_BILINEAR, dft=dft)
+            ctx = emg.Context(w.pos, d_dev, n, n, params, obj=torch.ones((n, n), dtype=torch.complex64),
+                              probe=torch.from_numpy(w.q_init_blurred.astype(np.complex64)), stream=stream)
+            emg.emg_normalize_probe(ctx.ctx)
+            torch.cuda.synchronize()
+            z_init, q_init = ctx.obj.clone(), ctx.probe.clone()
+            for e in range(args.warmup):
+                emg.emg_run_epochs(ctx.ctx, 1, order=orders[e])
+            emg.emg_profile_read(ctx.ctx)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            clocks = ClockSampler(local)
+            clocks.start()
+            torch.cuda.synchronize()
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+                emg.emg_run_epochs(ctx.ctx, 1, order=orders[args.warmup + i])
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            clk = clocks.stop()
+            ms = sum(a.elapsed_time(b) for a, b in ev)
+            counts = emg.emg_profile_read(ctx.ctx)
+            # per-kind event times over two more epochs of direct launches
+            emg.emg_set_profiling(ctx.ctx, True)
+            emg.emg_profile_read(ctx.ctx)
+            for e in range(2):
+                flush.fill_(float(e))
+                emg.emg_run_epochs(ctx.ctx, 1, order=orders[e])
+            prof = emg.emg_profile_read(ctx.ctx)
+            emg.emg_set_profiling(ctx.ctx, False)
+            # time to the oracle's misfit, from the initial state, epochs timed alone
+            ttt = None
+            if max_epochs:
+                ctx.obj.copy_(z_init)
+                ctx.probe.copy_(q_init)
+                emg.emg_set_epoch(ctx.ctx, 0)
+                t_ms, phis = 0.0, []
+                for e in range(max_epochs):
+                    flush.fill_(float(e))
+                    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a0.record(stream)
+                    emg.emg_run_epochs(ctx.ctx, 1, order=orders[e])
+                    a1.record(stream)
+                    phi = emg.emg_misfit(ctx.ctx)
+                    t_ms += a0.elapsed_time(a1)
+                    phis.append(phi)
+                    if phi <= phi_target:
+                        ttt = {"ms": round(t_ms, 3), "epochs": e + 1, "phi": phi}
+                        break
+                if ttt is None:
+                    ttt = {"ms": None, "epochs": None, "phi_after": phis}
+            res[name] = dict(value=N * args.steps / (ms / 1e3), ms_per_epoch=ms / args.steps, counts=counts,
+                             prof=prof, clocks=clk, ttt=ttt, ctx=ctx)
+        # end to end on host buffers through the tensor-core variant
+        ctx = res["bf16x3"]["ctx"]
+        d_pin = torch.from_numpy(d).pin_memory()
+        z_pin = torch.ones((n, n), dtype=torch.complex64).pin_memory()
+        q_pin = q_init.cpu().pin_memory()
+        dn, zn, qn = d_pin.numpy(), z_pin.numpy(), q_pin.numpy()
+        emg.emg_reconstruct_host(ctx.ctx, dn, zn, qn, 1, running=True)
+        t_e2e = 0.0
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            emg.emg_reconstruct_host(ctx.ctx, dn, zn, qn, 1, running=True)
+            t_e2e += time.perf_counter() - t0
+    tc = res["bf16x3"]
+    dft_ms, dft_launches = tc["prof"]["dft"]
+    # executed MMA work of the four GEMM passes: 2 (b m) (2m) (2m) flops per pass and product, 3 products
+    flops_epoch = 4 * 2 * N * m * (2 * m) * (2 * m) * 3
+    achieved = flops_epoch * 2 / (dft_ms / 1e3) / 1e12
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    line = {
+        "metric": "scan positions/sec per eMAGPIE epoch (DFT pair on tensor cores, BF16 x3 split)",
+        "value": tc["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tc["ms_per_epoch"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3/f32", "data": "synthetic",
+        "config": {"workload": f"{PREC_WORKLOAD}: object {n}^2, probe {m}^2, {N} positions (64x64 raster, step 28, "
+                               f"+-3 px), Poisson peak 1e5, {p['levels']} levels bilinear, minibatch {B}",
+                   "l2": "flushed (256 MB write) before every timed epoch; amplitudes 1.07 GB > L2"},
+        "fft32": {"value": res["fft32"]["value"], "ms_per_epoch": res["fft32"]["ms_per_epoch"]},
+        "time_to_oracle_misfit": {"target": {"epochs": e_target, "phi": phi_target},
+                                  "bf16x3": tc["ttt"], "fft32": res["fft32"]["ttt"]},
+        "e2e": {"value": N * args.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(dn.nbytes + zn.nbytes +
+                                                                                          qn.nbytes),
+                "d2h_bytes_per_step": int(zn.nbytes + qn.nbytes + 8)},
+        "gpu_launches": sum(v[1] for v in tc["counts"].values()),
+        "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 5), "peak_source": "measured (bf16, sustained)",
+                     "traffic": None, "kernel": "k_tc_dft x4 + k_tc_psi (tensor-core DFT chain)",
+                     "flops_per_minibatch": 4 * 2 * B * m * (2 * m) * (2 * m) * 3,
+                     "timing": f"CUDA events around each minibatch's DFT chain over 2 epochs "
+                               f"({dft_ms / 2:.3f} ms/epoch of {tc['ms_per_epoch']:.3f})"},
+        "clocks": tc["clocks"],
+    }
+    if not args.no_cpu_baseline:
+        rate, done, dt = cpu_oracle_sample(w, d, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{done} positions from the initial state, {dt:.1f} s single-thread FP64"}
+    print(json.dumps(line), flush=True)
+    for r in res.values():
+        r["ctx"].close()
+
+
 def batch_problems(count: int = 64, seed: int = 1003):
     """64 uneven problems: object side from {256, 512, 768, 1024}, probe side from
     {64, 128, 256} with m <= n/2, 100-2500 positions (raster step m/8, +-2 px
@@ -609,6 +755,9 @@ def main():
         return
     if args.workload == "batch64":
         run_gpu_batch(args, world, rank, local)
+        return
+    if args.workload == PREC_WORKLOAD:
+        run_gpu_prec(args, world, rank, local)
         return
     run_gpu(args, world, rank, local)
 

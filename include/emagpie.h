@@ -51,6 +51,7 @@ typedef enum emg_status {
 enum { EMG_PROLONG_CONST = 0, EMG_PROLONG_BILINEAR = 1 };
 enum { EMG_COMBINE_WAVG = 0, EMG_COMBINE_SUM = 1 };
 enum { EMG_SCATTER_DETERMINISTIC = 0, EMG_SCATTER_ATOMIC = 1 };
+enum { EMG_DFT_FFT32 = 0, EMG_DFT_BF16X3 = 1 };
 
 /* Same object as cudaStream_t; NULL is the legacy default stream. */
 typedef struct CUstream_st* emg_stream_t;
@@ -94,6 +95,12 @@ typedef struct emg_problem {
  *  joint      1: geometric-mean joint step (eMAGPIE); 0: take z+ and Q+ as they
  *             are (the rPIE-style simultaneous update of Sec. 2.2).
  *  w_eps      weight floor of the object combine, relative to max|Q|^2, >= 0.
+ *  dft        EMG_DFT_FFT32: the FFT pair a2 / a4 as FP32 shared-memory FFTs
+ *             inside the step kernel (default);
+ *             EMG_DFT_BF16X3: the pair as tensor-core GEMMs in BF16 with every
+ *             operand split into high and low parts (see emg_dft2_bf16x3);
+ *             m = 128 or 256 only (EMG_ENOTSUP otherwise).  The misfit of
+ *             emg_misfit is always evaluated on the FP32 path.
  *  seed       schedule seed used when emg_run_epochs gets no order array.
  */
 typedef struct emg_params {
@@ -105,10 +112,12 @@ typedef struct emg_params {
   int32_t scatter;
   int32_t joint;
   float w_eps;
+  int32_t dft;
   uint64_t seed;
 } emg_params;
 
-/* Fills *p with alpha 0.01, L 1, B 1, CONST, WAVG, DETERMINISTIC, joint 1, w_eps 1e-6, seed 0. */
+/* Fills *p with alpha 0.01, L 1, B 1, CONST, WAVG, DETERMINISTIC, joint 1, w_eps 1e-6,
+ * EMG_DFT_FFT32, seed 0. */
 emg_status emg_default_params(emg_params* p);
 
 /* Human-readable name of a status code (static string). */
@@ -289,9 +298,10 @@ void emg_batch_destroy(emg_batch* batch);
  * Kernel timing for measurement (not part of the method).  enable = 1 makes
  * every later launch of the minibatch path record a pair of CUDA events on the
  * context's stream.  emg_profile_read synchronises and returns, per kernel
- * kind {probe prep, per-position step, combine, other}, the summed event time
- * in milliseconds (ms[4], host) and the number of launches (launches[4], host;
- * counted whether or not profiling is on) since the last read, then resets.
+ * kind {probe prep, per-position step, combine, other, tensor-core DFT passes},
+ * the summed event time in milliseconds (ms[5], host) and the number of
+ * launches (launches[5], host; counted whether or not profiling is on) since
+ * the last read, then resets.
  */
 emg_status emg_set_profiling(emg_ctx* ctx, int32_t enable);
 emg_status emg_profile_read(emg_ctx* ctx, double* ms, int64_t* launches);
@@ -310,7 +320,8 @@ emg_status emg_profile_read(emg_ctx* ctx, double* ms, int64_t* launches);
  *  intensity   device float32 [n_pos][m][m] data d_k in natural order (DC at [0][0])
  *  idx, b      host int32 [b] positions of this minibatch, 1 <= b <= n_pos
  *  m           16, 32, 64 or 128 (EMG_ENOTSUP for 256)
- *  params      as for emg_create (minibatch and seed are ignored)
+ *  params      as for emg_create (minibatch and seed are ignored; dft must be
+ *              EMG_DFT_FFT32, EMG_ENOTSUP for EMG_DFT_BF16X3)
  *
  * The result equals emg_step_minibatch on the same inputs.  Its only scratch
  * is one fixed device array of EMG_NOALLOC_SCRATCH_BYTES per GPU, part of the

@@ -21,7 +21,7 @@ from . import build as _build
 __all__ = [
     "EMG_OK", "EMG_EINVAL", "EMG_ENOMEM", "EMG_ECUDA", "EMG_ETIMEOUT", "EMG_ENOTSUP",
     "EMG_PROLONG_CONST", "EMG_PROLONG_BILINEAR", "EMG_COMBINE_WAVG", "EMG_COMBINE_SUM",
-    "EMG_SCATTER_DETERMINISTIC", "EMG_SCATTER_ATOMIC", "EmgError", "EmgProblem", "EmgParams",
+    "EMG_SCATTER_DETERMINISTIC", "EMG_SCATTER_ATOMIC", "EMG_DFT_FFT32", "EMG_DFT_BF16X3", "EmgError", "EmgProblem", "EmgParams",
     "build", "load", "lib_path", "exported_symbols", "emg_default_params", "emg_status_string",
     "emg_create", "emg_set_intensity", "emg_bind_state", "emg_normalize_probe",
     "emg_step_minibatch", "emg_position_stats", "emg_set_verify", "emg_run_epochs", "emg_misfit",
@@ -37,6 +37,7 @@ EMG_OK, EMG_EINVAL, EMG_ENOMEM, EMG_ECUDA, EMG_ETIMEOUT, EMG_ENOTSUP = range(6)
 EMG_PROLONG_CONST, EMG_PROLONG_BILINEAR = 0, 1
 EMG_COMBINE_WAVG, EMG_COMBINE_SUM = 0, 1
 EMG_SCATTER_DETERMINISTIC, EMG_SCATTER_ATOMIC = 0, 1
+EMG_DFT_FFT32, EMG_DFT_BF16X3 = 0, 1
 
 _STATUS_NAMES = ["EMG_OK", "EMG_EINVAL", "EMG_ENOMEM", "EMG_ECUDA", "EMG_ETIMEOUT", "EMG_ENOTSUP"]
 
@@ -56,7 +57,8 @@ class EmgProblem(ctypes.Structure):
 class EmgParams(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_float), ("levels", ctypes.c_int32), ("minibatch", ctypes.c_int32),
                 ("prolong", ctypes.c_int32), ("combine", ctypes.c_int32), ("scatter", ctypes.c_int32),
-                ("joint", ctypes.c_int32), ("w_eps", ctypes.c_float), ("seed", ctypes.c_uint64)]
+                ("joint", ctypes.c_int32), ("w_eps", ctypes.c_float), ("dft", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -324,13 +326,13 @@ def emg_set_profiling(ctx: int, enable: bool) -> None:
     _check(load().emg_set_profiling(ctx, int(bool(enable))), "emg_set_profiling", ctx)
 
 
-PROFILE_KINDS = ("prep", "step", "apply", "other")
+PROFILE_KINDS = ("prep", "step", "apply", "other", "dft")
 
 
 def emg_profile_read(ctx: int):
     """Returns {kind: (milliseconds, launches)} since the last read."""
-    ms = np.zeros(4, dtype=np.float64)
-    n = np.zeros(4, dtype=np.int64)
+    ms = np.zeros(len(PROFILE_KINDS), dtype=np.float64)
+    n = np.zeros(len(PROFILE_KINDS), dtype=np.int64)
     _check(load().emg_profile_read(ctx, ms.ctypes.data_as(_F64P),
                                    n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
            "emg_profile_read", ctx)

@@ -48,7 +48,13 @@ def _digest(extra_flags) -> str:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compiles the library if needed and returns its path."""
+    """Compiles the library if needed and returns its path.
+
+    Extra nvcc flags come from ``extra_flags`` and the environment variable
+    EMG_NVCC_EXTRA (whitespace-separated, e.g. tuning macros such as
+    -DEMG_UPDATE_GROUP=8); both are part of the build stamp.
+    """
+    extra_flags = list(extra_flags) + os.environ.get("EMG_NVCC_EXTRA", "").split()
     os.makedirs(OUT_DIR, exist_ok=True)
     stamp = os.path.join(OUT_DIR, "build.sha256")
     digest = _digest(extra_flags)

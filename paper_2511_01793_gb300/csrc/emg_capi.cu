@@ -18,7 +18,7 @@ using emg::PrepArgs;
 using emg::StepArgs;
 
 // Kernel kinds counted and timed by the profiling hooks.
-enum { kKindPrep = 0, kKindStep = 1, kKindApply = 2, kKindOther = 3, kKinds = 4 };
+enum { kKindPrep = 0, kKindStep = 1, kKindApply = 2, kKindOther = 3, kKindDft = 4, kKinds = 5 };
 
 struct emg_ctx {
   int device = 0;
@@ -56,7 +56,7 @@ struct emg_ctx {
   float2* graph_probe = nullptr;
   int graph_verify = -1;
   int graph_cluster = -1;
-  int64_t graph_counts[4] = {0, 0, 0, 0};
+  int64_t graph_counts[kKinds] = {0, 0, 0, 0, 0};
   float* d_wq = nullptr;          // [m][m]
   void* d_levels = nullptr;       // all multigrid arrays
   int32_t* d_orders = nullptr;    // [cap_orders]
@@ -73,7 +73,13 @@ struct emg_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;
   size_t ev_used = 0;
-  int64_t launches[kKinds] = {0, 0, 0, 0};
+  int64_t launches[kKinds] = {0, 0, 0, 0, 0};
+
+  // tensor-core DFT path (par.dft == EMG_DFT_BF16X3)
+  emg::TcWork* tc = nullptr;
+  float* d_amp_t = nullptr;       // [N][m][m] a_k transposed
+  float2* d_tc_r = nullptr;       // [B][m][m] R_k
+  double* d_tc_part = nullptr;    // [B][tiles] misfit partial sums
 
   std::vector<int32_t> h_pos;
   PrepArgs prep{};
@@ -135,8 +141,8 @@ struct LaunchMark {
   emg_ctx* c;
   int kind;
   cudaEvent_t stop = nullptr;
-  LaunchMark(emg_ctx* ctx, int k) : c(ctx), kind(k) {
-    c->launches[k] += 1;
+  LaunchMark(emg_ctx* ctx, int k, int n = 1) : c(ctx), kind(k) {
+    c->launches[k] += n;
     if (!c->profile) return;
     if (c->ev_used + 2 > c->ev_pool.size()) {
       for (int i = 0; i < 64; ++i) {
@@ -181,6 +187,9 @@ emg_status validate_params(emg_ctx* c, const emg_params* p, int m, int n_pos) {
   if (p->scatter != EMG_SCATTER_DETERMINISTIC) return fail(c, EMG_EINVAL, "unknown scatter mode");
   if (p->joint != 0 && p->joint != 1) return fail(c, EMG_EINVAL, "joint must be 0 or 1");
   if (!(p->w_eps >= 0.f) || !isfinite(p->w_eps)) return fail(c, EMG_EINVAL, "w_eps must be finite and >= 0");
+  if (p->dft != EMG_DFT_FFT32 && p->dft != EMG_DFT_BF16X3) return fail(c, EMG_EINVAL, "unknown dft mode");
+  if (p->dft == EMG_DFT_BF16X3 && !emg::tc_supported(m))
+    return fail(c, EMG_ENOTSUP, "the tensor-core DFT is built for m = 128 and 256");
   if (!emg::step_supported(m, p->levels, emg::default_cluster(m)))
     return fail(c, EMG_ENOTSUP, "too many multigrid levels for this probe size");
   return EMG_OK;
@@ -216,6 +225,11 @@ void free_all(emg_ctx* c) {
   cudaFree(c->d_own_object);
   cudaFree(c->d_own_probe);
   if (c->h_scalar) cudaFreeHost(c->h_scalar);
+  emg::tc_work_destroy(c->tc);
+  c->tc = nullptr;
+  cudaFree(c->d_amp_t);
+  cudaFree(c->d_tc_r);
+  cudaFree(c->d_tc_part);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
 }
@@ -358,7 +372,31 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   sa.mu = c->d_mu;
   sa.phi = d_phi_out;
   sa.phi_after = c->d_phi_after;
-  {
+  if (c->tc) {
+    emg::TcStepArgs ta{};
+    ta.object = c->object;
+    ta.probe = c->probe;
+    ta.pos = c->d_pos;
+    ta.order = d_idx;
+    ta.n_rows = c->n_rows;
+    ta.n_cols = c->n_cols;
+    ta.b = b;
+    ta.amp_t = c->d_amp_t;
+    ta.R = c->d_tc_r;
+    ta.partial = c->d_tc_part;
+    {
+      LaunchMark mk(c, kKindDft, 5);
+      e = emg::tc_exit_waves(c->tc, ta, strm);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core DFT launch");
+    sa.r_in = c->d_tc_r;
+    sa.r_partial = c->d_tc_part;
+    sa.r_tiles = emg::tc_tiles_per_position(c->m);
+    {
+      LaunchMark mk(c, kKindStep);
+      e = emg::launch_step_rin(c->m, b, sa, strm);
+    }
+  } else {
     LaunchMark mk(c, kKindStep);
     e = emg::launch_step(c->m, b, sa, strm);
   }
@@ -385,6 +423,16 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
     e = emg::launch_apply(aa, strm);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_apply launch");
+  return EMG_OK;
+}
+
+// Reads (synchronously) the flag the tensor-core kernels set when one of their
+// bounded waits gave up; callers invoke it where they synchronise anyway.
+emg_status check_tc_flag(emg_ctx* c) {
+  if (!c->tc) return EMG_OK;
+  int flag = 0;
+  EMG_CUDA(c, cudaMemcpy(&flag, emg::tc_error_flag(c->tc), sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) return fail(c, EMG_ETIMEOUT, "a bounded wait in the tensor-core DFT kernel gave up");
   return EMG_OK;
 }
 
@@ -507,8 +555,11 @@ emg_status run_epochs_impl(emg_ctx* c, int32_t n_epochs, const int32_t* order, d
   if (misfit)
     EMG_CUDA(c, cudaMemcpyAsync(misfit, c->d_hist + c->cap_hist, n_epochs * sizeof(double),
                                 cudaMemcpyDeviceToHost, c->stream));
-  if (running || misfit) EMG_CUDA(c, cudaStreamSynchronize(c->stream));
-  else EMG_CUDA(c, cudaGetLastError());
+  if (running || misfit) {
+    EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_tc_flag(c);
+  }
+  EMG_CUDA(c, cudaGetLastError());
   return EMG_OK;
 }
 
@@ -532,6 +583,10 @@ emg_status set_intensity_impl(emg_ctx* c, const float* intensity) {
   }
   cudaError_t e = emg::launch_amp_prep(src, c->d_amp, c->m, c->n_pos, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "k_amp_prep launch");
+  if (c->tc) {
+    e = emg::launch_tc_amp(src, c->d_amp_t, c->m, c->n_pos, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "k_tc_amp launch");
+  }
   return EMG_OK;
 }
 
@@ -549,6 +604,7 @@ emg_status emg_default_params(emg_params* p) {
   p->scatter = EMG_SCATTER_DETERMINISTIC;
   p->joint = 1;
   p->w_eps = 1e-6f;
+  p->dft = EMG_DFT_FFT32;
   p->seed = 0;
   return EMG_OK;
 }
@@ -606,6 +662,11 @@ emg_status emg_create(emg_ctx** out, const emg_problem* pr, const emg_params* pa
   if (cudaMallocHost(&c->h_scalar, 64 * sizeof(double)) != cudaSuccess) return bail(EMG_ENOMEM);
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(EMG_ECUDA);
   if (alloc_levels(c) != EMG_OK) return bail(EMG_ENOMEM);
+  if (par->dft == EMG_DFT_BF16X3) {
+    if (emg::tc_work_create(&c->tc, m, B) != cudaSuccess || dmalloc(&c->d_amp_t, (size_t)N * mm) ||
+        dmalloc(&c->d_tc_r, (size_t)B * mm) || dmalloc(&c->d_tc_part, (size_t)B * emg::tc_tiles_per_position(m)))
+      return bail(EMG_ENOMEM);
+  }
   c->h_pos.resize((size_t)2 * N);
   if (cudaMemcpyAsync(c->h_pos.data(), pr->pos, c->h_pos.size() * sizeof(int32_t), cudaMemcpyDefault,
                       c->stream) != cudaSuccess ||
@@ -669,6 +730,7 @@ emg_status emg_step_minibatch(emg_ctx* c, const int32_t* idx, int32_t b, double*
     EMG_CUDA(c, cudaMemcpyAsync(c->h_scalar, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     EMG_CUDA(c, cudaStreamSynchronize(c->stream));
     *sampled_misfit = c->h_scalar[0];
+    return check_tc_flag(c);
   }
   return EMG_OK;
 }
@@ -720,7 +782,7 @@ emg_status emg_misfit(emg_ctx* c, double* out) {
   EMG_CUDA(c, cudaMemcpyAsync(c->h_scalar, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   EMG_CUDA(c, cudaStreamSynchronize(c->stream));
   *out = c->h_scalar[0];
-  return EMG_OK;
+  return check_tc_flag(c);
 }
 
 emg_status emg_set_epoch(emg_ctx* c, int64_t epoch) {
@@ -1081,7 +1143,7 @@ emg_status emg_profile_read(emg_ctx* c, double* ms, int64_t* launches) {
   if (!ms || !launches) return fail(c, EMG_EINVAL, "NULL output");
   DeviceGuard g(c->device);
   EMG_CUDA(c, cudaStreamSynchronize(c->stream));
-  double acc[kKinds] = {0, 0, 0, 0};
+  double acc[kKinds] = {0, 0, 0, 0, 0};
   for (auto& mk : c->ev_marks) {
     float t = 0.f;
     EMG_CUDA(c, cudaEventElapsedTime(&t, mk.second.first, mk.second.second));

@@ -612,6 +612,11 @@ __global__ void __launch_bounds__(StepThreads<M>::value) k_step(const StepArgs a
 // slab, so a minibatch of B positions occupies C B SMs.
 namespace cg = cooperative_groups;
 
+// Pixels per unrolled group in the update pass of the cluster step kernel.
+#ifndef EMG_UPDATE_GROUP
+#define EMG_UPDATE_GROUP 16
+#endif
+
 template <int M> struct ClusterSize;
 template <> struct ClusterSize<16> { static constexpr int value = 2; };
 template <> struct ClusterSize<32> { static constexpr int value = 2; };
@@ -905,18 +910,22 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
   float2* qt = a.qt + (size_t)kb * M * M;
   const float2* Z1 = Zl[1];
   float acc_after = 0.f;
-  float2 qv[PER];
+  // Groups of UG pixels: the probe loads of a group are issued together, and
+  // the loop body stays small enough for the instruction cache.
+  constexpr int UG0 = EMG_UPDATE_GROUP < PER ? EMG_UPDATE_GROUP : PER;
+  constexpr int UG = PER % UG0 == 0 ? UG0 : 1;
+#pragma unroll 1
+  for (int t0 = 0; t0 < PER; t0 += UG) {
+  float2 qv[UG];
 #pragma unroll
-  for (int t = 0; t < PER; ++t) {
-    const int p = tid + t * NT;
-    qv[t] = __ldg(a.probe + row0 * M + p);
-  }
+  for (int u = 0; u < UG; ++u) qv[u] = __ldg(a.probe + row0 * M + tid + (t0 + u) * NT);
 #pragma unroll
-  for (int t = 0; t < PER; ++t) {
+  for (int u = 0; u < UG; ++u) {
+    const int t = t0 + u;
     const int p = tid + t * NT;
     const int lr = p / M, c = p % M, r = row0 + lr;
     const float2 zk = zbuf[p];
-    const float2 q = qv[t];
+    const float2 q = qv[u];
     const float2 R = rowbuf[lr * SR + c];
     const float2 res = csub(R, cmul(q, zk));
     const float a2 = cabs2(q);
@@ -942,6 +951,7 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
     zt[r * M + c] = zn;
     qt[r * M + c] = qn;
     if (a.verify) acc_after += cabs2(csub(cmul(qn, zn), R));
+  }
   }
   if (a.verify) {
     const double part = 0.5 * block_sum_f<NT>(acc_after, redf, redd);
@@ -2085,6 +2095,7 @@ extern "C" emg_status emg_step_minibatch_noalloc(float* object, int32_t n_rows, 
   if (p->combine != EMG_COMBINE_WAVG && p->combine != EMG_COMBINE_SUM) return EMG_EINVAL;
   if (p->joint != 0 && p->joint != 1) return EMG_EINVAL;
   if (p->scatter != EMG_SCATTER_DETERMINISTIC) return EMG_ENOTSUP;
+  if (p->dft != EMG_DFT_FFT32) return p->dft == EMG_DFT_BF16X3 ? EMG_ENOTSUP : EMG_EINVAL;
   if (step_smem_bytes(m, p->levels) > (size_t)step_smem_limit()) return EMG_ENOTSUP;
   for (int i = 0; i < b; ++i)
     if (idx[i] < 0 || idx[i] >= n_pos) return EMG_EINVAL;

@@ -51,6 +51,12 @@ CONFIGS = {
         peak=1e4, alpha=0.05, minibatch=64, levels=3, prolong="bilinear",
         epochs=100, seed=1002,
     ),
+    # Precision case: the DFT pair on tensor cores (BF16 split) against FP32 FFTs.
+    "prec_n2048_m256": dict(
+        n=2048, m=256, side=64, step=28, jitter=3, radius=80.0, phi_max=math.pi,
+        peak=1e5, alpha=0.05, minibatch=256, levels=3, prolong="bilinear",
+        epochs=6, seed=1005,
+    ),
     # Differentiation case: gradient of the exit-wave misfit at full size.
     "grad_n1024_m256": dict(
         n=1024, m=256, side=40, step=20, jitter=2, radius=80.0, phi_max=math.pi,

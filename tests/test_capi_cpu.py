@@ -64,6 +64,8 @@ def _problem(m=32, n_pos=4):
     ("scatter", emg.EMG_SCATTER_ATOMIC, emg.EMG_ENOTSUP),
     ("joint", 2, emg.EMG_EINVAL),
     ("w_eps", -1.0, emg.EMG_EINVAL),
+    ("dft", 2, emg.EMG_EINVAL),
+    ("dft", emg.EMG_DFT_BF16X3, emg.EMG_ENOTSUP),   # m = 32: the tensor-core DFT needs m = 128 or 256
 ])
 def test_create_rejects_bad_parameters_before_any_launch(lib, field, value, expect):
     p = emg.emg_default_params()

@@ -74,3 +74,78 @@ def test_tc_dft2_of_a_delta_is_flat(lib, torch):
     u = np.arange(m)
     ref = np.exp(-2j * np.pi * (5 * u[:, None] + 9 * u[None, :]) / m)
     assert np.max(np.abs(got - ref)) <= 3 * U * U * 4
+
+
+# ---------------------------------------------------------------------------
+# The minibatch step with the tensor-core DFT pair (params.dft = EMG_DFT_BF16X3)
+
+from emg_cases import Case, covered_mask, make_context, oracle_inputs, oracle_params, rel_err, state  # noqa: E402
+
+# A step runs four 1-D passes (forward and inverse 2-D DFTs) whose relative
+# error is each below 3 u^2.  Every other operation is the FP32 path's, whose
+# error (about 1e-7 on these cases) is negligible beside it.  The modulus
+# replacement keeps the error's size (|a Psi/|Psi|| = a), and the gains of the
+# object and probe steps are at most 1.  The step's relative error is therefore
+# bounded by that of its exit waves: 4 * 3 u^2 = 1.8e-4.
+TC_STEP_TOL = 4 * 3 * U * U
+
+TC_CASES = [
+    # m, levels, prolong, n_batch
+    (128, 1, "const", 6),
+    (128, 3, "bilinear", 6),
+    (256, 2, "const", 3),
+    (256, 3, "bilinear", 4),
+]
+
+
+def _step_both(lib, m, levels, prolong, nb):
+    case = Case(n=2 * m + 40, m=m, side=4, noise_peak=1e5, seed=m + levels)
+    p = oracle_params(alpha=0.05, levels=levels, minibatch=nb, prolong=prolong)
+    rng = np.random.default_rng(m * 10 + levels)
+    idx = list(rng.permutation(case.n_pos - 4)[: nb - 2]) + [case.n_pos - 4, case.n_pos - 3]
+    out = {}
+    for dft in (0, 1):
+        ctx = make_context(lib, case, p, dft=dft)
+        lib.emg_set_verify(ctx.ctx, True)
+        sampled = lib.emg_step_minibatch(ctx.ctx, idx, want_misfit=True)
+        z, q = state(ctx)
+        out[dft] = (z, q, sampled, lib.emg_position_stats(ctx.ctx, nb))
+        ctx.close()
+    zo, qo, pos, a, po = oracle_inputs(case, p)
+    info = {}
+    z_o, q_o = O.minibatch_step(zo, qo, pos, a, idx, po, out=info)
+    return case, idx, out, (z_o, q_o, info)
+
+
+@pytest.mark.parametrize("m,levels,prolong,nb", TC_CASES)
+def test_tc_step_matches_the_oracle(lib, torch, m, levels, prolong, nb):
+    case, idx, out, (z_o, q_o, info) = _step_both(lib, m, levels, prolong, nb)
+    mask = covered_mask(case, idx)
+    z_t, q_t, sampled, stats = out[1]
+    z_f, q_f, _, _ = out[0]
+    e_tc = (rel_err(z_t, z_o, mask), rel_err(q_t, q_o))
+    e_fft = (rel_err(z_f, z_o, mask), rel_err(q_f, q_o))
+    print(f"m={m} L={levels}: tc {e_tc[0]:.2e} {e_tc[1]:.2e}  fft {e_fft[0]:.2e} {e_fft[1]:.2e}  "
+          f"sampled {abs(sampled - info['sampled_misfit']) / info['sampled_misfit']:.2e}")
+    assert e_tc[0] <= TC_STEP_TOL and e_tc[1] <= TC_STEP_TOL
+    assert np.array_equal(z_t[~mask], case.z0.astype(np.complex128)[~mask])
+    assert abs(sampled - info["sampled_misfit"]) <= TC_STEP_TOL * info["sampled_misfit"]
+    for i, st in enumerate(info["positions"]):
+        assert abs(stats[i, 2] - st["mu"]) <= 1e-6 * st["mu"]
+        assert abs(stats[i, 0] - st["surrogate_before"]) <= TC_STEP_TOL * st["surrogate_before"]
+        assert abs(stats[i, 1] - st["surrogate_after"]) <= TC_STEP_TOL * st["surrogate_before"]
+
+
+def test_tc_epochs_are_bitwise_repeatable(lib, torch):
+    m = 128
+    case = Case(n=2 * m + 40, m=m, side=4, noise_peak=1e5, seed=3)
+    p = oracle_params(alpha=0.05, levels=3, minibatch=8, prolong="bilinear")
+    res = []
+    for _ in range(2):
+        ctx = make_context(lib, case, p, dft=1)
+        mis = lib.emg_run_epochs(ctx.ctx, 2, misfit=True)
+        z, q = state(ctx)
+        res.append((z, q, mis))
+        ctx.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert np.array_equal(res[0][2][1], res[1][2][1])
