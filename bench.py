@@ -39,6 +39,7 @@ METRIC = "scan positions/sec per eMAGPIE epoch"
 UNIT = "positions/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_stepc_mg_n512_m128.md")
+CLUSTER = 4   # CTAs per position of the step kernel (the library's default for m = 128)
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2511_01793_gb300", "csrc", f)
                   for f in ("emg_kernels.cu", "emg_fft.cuh")]
 
@@ -278,6 +279,7 @@ def run_gpu(args, world, rank, local):
         ctx = emg.Context(w.pos, d, p["n"], p["n"], params, obj=torch.from_numpy(z0),
                           probe=torch.from_numpy(q0), stream=stream)
         emg.emg_normalize_probe(ctx.ctx)
+        emg.emg_set_cluster(ctx.ctx, CLUSTER)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
         def barrier():
@@ -358,7 +360,7 @@ def run_gpu(args, world, rank, local):
     kernel_share = {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4) for k, v in prof.items()}
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 5), "peak_source": peak_kind,
-                "traffic": traffic, "kernel": "k_stepc<128,2>",
+                "traffic": traffic, "kernel": f"k_stepc<{m},{CLUSTER}>",
                 "algorithmic_bytes_per_launch": int(alg_bytes_per_pos * pos_per_launch),
                 "avg_launch_us": round(avg_launch_s * 1e6, 3), "launch_share": kernel_share,
                 "timing": "CUDA events around each k_step launch over a second pass of the same "

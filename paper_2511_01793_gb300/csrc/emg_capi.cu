@@ -190,7 +190,7 @@ emg_status validate_params(emg_ctx* c, const emg_params* p, int m, int n_pos) {
   if (p->dft != EMG_DFT_FFT32 && p->dft != EMG_DFT_BF16X3) return fail(c, EMG_EINVAL, "unknown dft mode");
   if (p->dft == EMG_DFT_BF16X3 && !emg::tc_supported(m))
     return fail(c, EMG_ENOTSUP, "the tensor-core DFT is built for m = 128 and 256");
-  if (!emg::step_supported(m, p->levels, emg::default_cluster(m)))
+  if (!emg::step_supported(m, p->levels, emg::default_cluster(m, p->levels)))
     return fail(c, EMG_ENOTSUP, "too many multigrid levels for this probe size");
   return EMG_OK;
 }
@@ -640,7 +640,7 @@ emg_status emg_create(emg_ctx** out, const emg_problem* pr, const emg_params* pa
   c->m = pr->m;
   c->n_pos = pr->n_pos;
   c->par = *par;
-  c->cluster = emg::default_cluster(pr->m);
+  c->cluster = emg::default_cluster(pr->m, par->levels);
   c->stream = (cudaStream_t)stream;
   auto bail = [&](emg_status s) {
     free_all(c);

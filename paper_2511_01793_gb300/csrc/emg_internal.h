@@ -118,7 +118,7 @@ struct GradReduceArgs {
 cudaError_t launch_gradient(int m, int b, const GradArgs& a, cudaStream_t s);
 cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t s);
 bool step_supported(int m, int levels, int cluster);
-int default_cluster(int m);
+int default_cluster(int m, int levels);
 // Copies, for each of `count` problems, its order row `*epoch` into its epoch buffer.
 cudaError_t launch_batch_orders(const int32_t* const* src, int32_t* const* dst, const int* n, int count,
                                 const int* epoch, cudaStream_t s);

@@ -614,8 +614,17 @@ namespace cg = cooperative_groups;
 
 // Pixels per unrolled group in the update pass of the cluster step kernel.
 #ifndef EMG_UPDATE_GROUP
-#define EMG_UPDATE_GROUP 16
+#define EMG_UPDATE_GROUP 8
 #endif
+
+// Cluster barrier arrive without release semantics, for barriers that order
+// execution only (every CTA of the cluster resident; no CTA exits while a
+// neighbour still reads its shared memory).  A release arrive would first
+// wait for all of the thread's outstanding loads and stores.
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;" ::: "memory"); }
 
 template <int M> struct ClusterSize;
 template <> struct ClusterSize<16> { static constexpr int value = 2; };
@@ -717,7 +726,7 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
   pdl_trigger();
   pdl_wait();  // object, probe, max|Q|^2 and level arrays come from earlier kernels
   const float MQ = __uint_as_float(*a.mq);
-  cl.barrier_arrive();  // completed (wait) before the first distributed shared memory access
+  cluster_arrive_relaxed();  // completed (wait) before the first distributed shared memory access
 
   // a1: gather my rows, psi = Q z_k, partial mu_k
   float mu_l = 0.f;
@@ -957,7 +966,14 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
     const double part = 0.5 * block_sum_f<NT>(acc_after, redf, redd);
     if (tid == 0) cluster_publish<C>(cl, rank, xd2, part);
   }
-  cl.sync();  // neighbours may still read my coarse rows; also publishes xd2
+  // Neighbours may still read my coarse rows: no CTA leaves before all arrive.
+  // The verify mode also publishes xd2, which needs the release / acquire pair.
+  if (a.verify) {
+    cl.sync();
+  } else {
+    cluster_arrive_relaxed();
+    cluster_wait();
+  }
   if (rank == 0 && tid == 0) {
     double phi = 0.0, after = 0.0;
 #pragma unroll
@@ -993,7 +1009,7 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_fwdc(const FwdArgs a) {
   const int tid = threadIdx.x;
   const int t = blockIdx.x / C;
   const int row0 = rank * H;
-  cl.barrier_arrive();
+  cluster_arrive_relaxed();
   if (MODE == 2) {
     const float2* x = a.in + (size_t)t * M * M;
     for (int p = tid; p < H * M; p += NT) rowbuf[(p / M) * SR + p % M] = x[row0 * M + p];
@@ -1057,7 +1073,7 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_ifftc(const FwdArgs a) {
   const int t = blockIdx.x / C;
   const float2* x = a.in + (size_t)t * M * M;
   const float sc = 1.f / (float)(M * M);
-  cl.barrier_arrive();
+  cluster_arrive_relaxed();
   for (int p = tid; p < M * H; p += NT) {
     const int er = p / H, lc = p % H, ec = rank * H + lc;
     colbuf[er * SC + lc] = cscale(x[(size_t)storage_to_freq<M>(er) * M + storage_to_freq<M>(ec)], sc);
@@ -1100,7 +1116,7 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_gradc(const GradArgs a) 
   const int k = a.first + kb;
   const int o_r = a.pos[2 * k], o_c = a.pos[2 * k + 1];
   const int row0 = rank * H;
-  cl.barrier_arrive();
+  cluster_arrive_relaxed();
   for (int p = tid; p < H * M; p += NT) {
     const int lr = p / M, c = p % M, r = row0 + lr;
     const float2 zk = gather_obj(a.object, a.n_rows, a.n_cols, o_r + r, o_c + c);
@@ -1854,7 +1870,14 @@ cudaError_t launch_step(int m, int b, const StepArgs& a, cudaStream_t s) {
   }
 }
 
-int default_cluster(int m) { return m <= 32 ? 1 : (m == 256 ? 8 : 2); }
+// CTAs per position by default: 4 for m = 128 where every CTA keeps a row at
+// the coarsest level (measured faster than 2), else the one choice built.
+int default_cluster(int m, int levels) {
+  if (m <= 32) return 1;
+  if (m == 256) return 8;
+  if (m == 128 && step_supported(m, levels, 4)) return 4;
+  return 2;
+}
 
 // Copies, per problem, the order row of the current epoch into the buffer its
 // captured minibatch kernels read.  One block per problem.
