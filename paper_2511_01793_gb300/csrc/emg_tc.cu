@@ -11,12 +11,14 @@
 // and can write them transposed per tile (the next pass then transforms the
 // other axis), replace the modulus (a3) or store FP32.
 //
-// One 128 x 256 output tile per CTA.  Warp 0 streams A and B chunks of 64 bf16
-// along K through a two-stage shared-memory ring with TMA (128-byte swizzle);
-// warp 1 owns 256 columns of tensor memory and issues tcgen05.mma from one lane;
-// warps 2-5 drain the accumulator with tcgen05.ld and run the epilogue.  Every
-// mbarrier wait is bounded in time: on expiry the kernel records an error flag,
-// waits (bounded) for what it issued, frees its tensor memory and returns.
+// Persistent kernel, one CTA per SM, looping over 128 x 256 output tiles.  Warp
+// 0 streams A and B chunks of 64 bf16 along K through a two-stage shared-memory
+// ring with TMA (128-byte swizzle); warp 1 owns all 512 columns of tensor memory
+// as two 256-column accumulators and issues tcgen05.mma from one lane; warps
+// 2-5 drain an accumulator with tcgen05.ld and run the epilogue while the MMAs
+// of the next tile fill the other one.  Every mbarrier wait is bounded in
+// time: on expiry the kernel records an error flag, waits (bounded) for what it
+// issued, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -41,7 +43,7 @@ constexpr int kTileB = kBN * kBK * 2;               // 32 KB
 constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;  // A hi, A lo, B hi, B lo
 constexpr int kTcSmem = kStages * kStageBytes + 1024;  // + alignment slack
 constexpr int kTcThreads = 192;
-constexpr uint32_t kTmemCols = kBN;
+constexpr uint32_t kTmemCols = 2 * kBN;             // two accumulators
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per wait
 
 // tcgen05.mma instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B
@@ -161,18 +163,23 @@ __device__ __forceinline__ void split_pair(float re, float im, uint32_t& hi, uin
 
 struct TcPassArgs {
   int m;                    // transform size; K = 2m, each tile has m rows
+  int tiles_n, tiles;       // output tiles along N, and in all
   uint32_t* out_hi;         // split outputs, bf16 pairs [rows][m]
   uint32_t* out_lo;
   float2* out_f32;          // FP32 outputs [rows][m]
   float scale;              // FP32 outputs: multiplier; modulus mode: 1/m^2 folded into Psi'
   const float* amp_t;       // modulus mode: a_k transposed, [N][m][m], a_k^T[v][u] = a_k[u][v]
   const int32_t* order;     // modulus mode: position of tile kb
-  double* partial;          // modulus mode: sum (|Psi| - a)^2 per CTA tile
+  double* partial;          // modulus mode: sum (|Psi| - a)^2 per output tile and epilogue warp
   int* err;                 // set to 1 when a bounded wait gives up
 };
 
 // Epilogue modes.
 enum { kEpiSplitT = 0, kEpiModulus = 1, kEpiF32 = 2, kEpiF32T = 3 };
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 template <int EPI>
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -180,18 +187,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
              const TcPassArgs a) {
   extern __shared__ uint8_t tc_smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[kStages];
-  __shared__ __align__(8) uint64_t empty_bar[kStages];
-  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ __align__(8) uint64_t full_bar[kStages];   // stage loaded (TMA bytes arrived)
+  __shared__ __align__(8) uint64_t empty_bar[kStages];  // stage consumed by the MMAs
+  __shared__ __align__(8) uint64_t accf_bar[2];         // accumulator complete
+  __shared__ __align__(8) uint64_t acce_bar[2];         // accumulator drained by the 4 epilogue warps
   __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_sh;
-  __shared__ double red_sh[4];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t raw = smem_u32(tc_smem_raw);
   const uint32_t tiles_s = (raw + 1023u) & ~1023u;
-  const int n_tile = blockIdx.x, m_tile = blockIdx.y;
   const int KC = 2 * a.m / kBK;
 
   if (threadIdx.x == 0) {
@@ -200,13 +206,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&acc_bar, 1);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf_bar[b], 1);
+      mbar_init(&acce_bar[b], 4);
+    }
     mbar_init(&drain_bar, 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (threadIdx.x < 4) red_sh[threadIdx.x] = 0.0;
   if (warp == 1) {
     __syncwarp();
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
@@ -221,55 +230,66 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
-      for (int kc = 0; kc < KC; ++kc) {
-        const int s = kc % kStages;
-        if (kc >= kStages && !mbar_wait(&empty_bar[s], ((kc / kStages) + 1) & 1, &abort_sh)) {
-          abort_sh = 1;
-          atomicExch(a.err, 1);
-          break;
+      uint32_t it = 0;  // chunks issued so far (the ring position runs on across tiles)
+      for (int t = blockIdx.x; t < a.tiles && !abort_sh; t += gridDim.x) {
+        const int m_tile = t / a.tiles_n, n_tile = t % a.tiles_n;
+        for (int kc = 0; kc < KC; ++kc, ++it) {
+          const uint32_t s = it % kStages;
+          if (it >= kStages && !mbar_wait(&empty_bar[s], ((it / kStages) + 1) & 1, &abort_sh)) {
+            abort_sh = 1;
+            atomicExch(a.err, 1);
+            break;
+          }
+          const uint32_t st = tiles_s + s * kStageBytes;
+          mbar_expect_tx(&full_bar[s], kStageBytes);
+          tma_load_2d(st, &mAh, &full_bar[s], kc * kBK, m_tile * kBM);
+          tma_load_2d(st + kTileA, &mAl, &full_bar[s], kc * kBK, m_tile * kBM);
+          tma_load_2d(st + 2 * kTileA, &mBh, &full_bar[s], kc * kBK, n_tile * kBN);
+          tma_load_2d(st + 2 * kTileA + kTileB, &mBl, &full_bar[s], kc * kBK, n_tile * kBN);
         }
-        if (abort_sh) break;
-        const uint32_t st = tiles_s + s * kStageBytes;
-        mbar_expect_tx(&full_bar[s], kStageBytes);
-        tma_load_2d(st, &mAh, &full_bar[s], kc * kBK, m_tile * kBM);
-        tma_load_2d(st + kTileA, &mAl, &full_bar[s], kc * kBK, m_tile * kBM);
-        tma_load_2d(st + 2 * kTileA, &mBh, &full_bar[s], kc * kBK, n_tile * kBN);
-        tma_load_2d(st + 2 * kTileA + kTileB, &mBl, &full_bar[s], kc * kBK, n_tile * kBN);
-        issued = kc + 1;
       }
       if (abort_sh) {  // let the copies already issued land before the CTA exits
         const volatile int never = 0;
-        for (int kc = issued > kStages ? issued - kStages : 0; kc < issued; ++kc)
-          mbar_wait(&full_bar[kc % kStages], (kc / kStages) & 1, &never);
+        for (uint32_t j = it > kStages ? it - kStages : 0; j < it; ++j)
+          mbar_wait(&full_bar[j % kStages], (j / kStages) & 1, &never);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       bool ok = true;
-      for (int kc = 0; kc < KC; ++kc) {
-        const int s = kc % kStages;
-        if (!mbar_wait(&full_bar[s], (kc / kStages) & 1, &abort_sh)) {
+      uint32_t it = 0;
+      int local = 0;
+      for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x, ++local) {
+        const int buf = local & 1;
+        if (local >= 2 && !mbar_wait(&acce_bar[buf], ((local >> 1) + 1) & 1, &abort_sh)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t st = tiles_s + s * kStageBytes;
+        const uint32_t d = tmem + (uint32_t)(buf * kBN);
+        for (int kc = 0; kc < KC; ++kc, ++it) {
+          const uint32_t s = it % kStages;
+          if (!mbar_wait(&full_bar[s], (it / kStages) & 1, &abort_sh)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = tiles_s + s * kStageBytes;
 #pragma unroll
-        for (int kk = 0; kk < kBK / 16; ++kk) {
-          const uint64_t ah = sw128_desc(st + kk * 32);
-          const uint64_t al = sw128_desc(st + kTileA + kk * 32);
-          const uint64_t bh = sw128_desc(st + 2 * kTileA + kk * 32);
-          const uint64_t bl = sw128_desc(st + 2 * kTileA + kTileB + kk * 32);
-          umma_bf16(tmem, ah, bh, (kc | kk) != 0);
-          umma_bf16(tmem, ah, bl, 1);
-          umma_bf16(tmem, al, bh, 1);
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            const uint64_t ah = sw128_desc(st + kk * 32);
+            const uint64_t al = sw128_desc(st + kTileA + kk * 32);
+            const uint64_t bh = sw128_desc(st + 2 * kTileA + kk * 32);
+            const uint64_t bl = sw128_desc(st + 2 * kTileA + kTileB + kk * 32);
+            umma_bf16(d, ah, bh, (kc | kk) != 0);
+            umma_bf16(d, ah, bl, 1);
+            umma_bf16(d, al, bh, 1);
+          }
+          umma_commit(&empty_bar[s]);
         }
-        umma_commit(&empty_bar[s]);
+        if (ok) umma_commit(&accf_bar[buf]);
       }
-      if (ok) {
-        umma_commit(&acc_bar);
-      } else {
+      if (!ok) {
         abort_sh = 1;
         atomicExch(a.err, 1);
         umma_commit(&drain_bar);  // every MMA issued so far completes before the TMEM is freed
@@ -279,24 +299,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else {
     const int q = warp & 3;  // this warp may access TMEM lanes 32 q .. 32 q + 31
-    const bool got = mbar_wait(&acc_bar, 0, &abort_sh);
-    const bool all = __all_sync(0xffffffffu, got);
-    if (!all) {
-      if (lane == 0) {
-        abort_sh = 1;
-        atomicExch(a.err, 1);
+    const int m = a.m;
+    int local = 0;
+    for (int t = blockIdx.x; t < a.tiles; t += gridDim.x, ++local) {
+      const int buf = local & 1;
+      const bool got = mbar_wait(&accf_bar[buf], (local >> 1) & 1, &abort_sh);
+      if (!__all_sync(0xffffffffu, got)) {
+        if (lane == 0) {
+          abort_sh = 1;
+          atomicExch(a.err, 1);
+        }
+        break;
       }
-    } else {
       tc_fence_after();
-      const int m = a.m;
+      const int m_tile = t / a.tiles_n, n_tile = t % a.tiles_n;
       const int gr = m_tile * kBM + q * 32 + lane;  // global row
       const int kb = gr / m, r = gr % m;
+      const uint32_t tb = tmem + (uint32_t)(buf * kBN) + ((uint32_t)(q * 32) << 16);
       float acc = 0.f;
 #pragma unroll 1
       for (int c0 = 0; c0 < kBN; c0 += 32) {
         float v[32];
         __syncwarp();
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        tmem_ld32(tb + (uint32_t)c0, v);
         const int u0 = (n_tile * kBN + c0) >> 1;  // first complex column of the chunk
         if constexpr (EPI == kEpiSplitT) {
 #pragma unroll
@@ -312,11 +337,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           float am[16];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const float4 t = __ldg(ap + j);
-            am[4 * j] = t.x;
-            am[4 * j + 1] = t.y;
-            am[4 * j + 2] = t.z;
-            am[4 * j + 3] = t.w;
+            const float4 t4 = __ldg(ap + j);
+            am[4 * j] = t4.x;
+            am[4 * j + 1] = t4.y;
+            am[4 * j + 2] = t4.z;
+            am[4 * j + 3] = t4.w;
           }
           uint32_t hi[16], lo[16];
 #pragma unroll
@@ -356,11 +381,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             a.out_f32[((size_t)kb * m + u0 + j) * m + r] = make_float2(v[2 * j] * a.scale, v[2 * j + 1] * a.scale);
         }
       }
+      // the accumulator is free for the tile after next once all four warps have read it
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce_bar[buf]);
       if constexpr (EPI == kEpiModulus) {
-        double d = (double)acc;
+        double dsum = (double)acc;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
-        if (lane == 0) red_sh[q] = d;
+        for (int off = 16; off > 0; off >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, off);
+        if (lane == 0) a.partial[(size_t)t * 4 + q] = dsum;
       }
     }
   }
@@ -370,10 +399,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncwarp();
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
-  }
-  if constexpr (EPI == kEpiModulus) {
-    if (threadIdx.x == 0)
-      a.partial[(size_t)m_tile * gridDim.x + n_tile] = ((red_sh[0] + red_sh[1]) + red_sh[2]) + red_sh[3];
   }
 }
 
@@ -546,8 +571,10 @@ cudaError_t get_tables(int m, const TcTables** out) {
 
 template <int EPI>
 cudaError_t launch_pass(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
-                        int rows, const TcPassArgs& a, cudaStream_t s) {
-  const dim3 grid(2 * a.m / kBN, rows / kBM);
+                        int rows, int sms, TcPassArgs a, cudaStream_t s) {
+  a.tiles_n = 2 * a.m / kBN;
+  a.tiles = a.tiles_n * (rows / kBM);
+  const int grid = a.tiles < sms ? a.tiles : sms;
   k_tc_dft<EPI><<<grid, kTcThreads, kTcSmem, s>>>(ah, al, bh, bl, a);
   return cudaGetLastError();
 }
@@ -579,6 +606,7 @@ struct TcWork {
   CUtensorMap amap[2][2];   // the two buffers as A operands
   const TcTables* tables = nullptr;
   int* d_err = nullptr;
+  int sms = 0;              // persistent grid: one CTA per SM
 };
 
 bool tc_supported(int m) { return m == 128 || m == 256; }
@@ -594,6 +622,12 @@ cudaError_t tc_work_create(TcWork** out, int m, int cap) {
   if (!w) return cudaErrorMemoryAllocation;
   w->m = m;
   w->cap = cap;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&w->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || w->sms < 1) {
+    delete w;
+    return cudaErrorInvalidDevice;
+  }
   const size_t pairs = (size_t)cap * m * m;
   cudaError_t e = get_tables(m, &w->tables);
   for (int i = 0; e == cudaSuccess && i < 2; ++i)
@@ -622,7 +656,7 @@ void tc_work_destroy(TcWork* w) {
 
 int* tc_error_flag(TcWork* w) { return w->d_err; }
 
-int tc_tiles_per_position(int m) { return (m / kBM) * (2 * m / kBN); }
+int tc_tiles_per_position(int m) { return (m / kBM) * (2 * m / kBN) * 4; }  // x 4 epilogue warps
 
 cudaError_t tc_dft2(TcWork* w, const float2* in, float2* out, int count, int inverse, cudaStream_t s) {
   if (count < 1 || count > w->cap) return cudaErrorInvalidValue;
@@ -638,11 +672,11 @@ cudaError_t tc_dft2(TcWork* w, const float2* in, float2* out, int count, int inv
   a.out_hi = w->buf[1][0];
   a.out_lo = w->buf[1][1];
   a.scale = 1.f;
-  if ((e = launch_pass<kEpiSplitT>(w->amap[0][0], w->amap[0][1], B[0], B[1], rows, a, s)) != cudaSuccess) return e;
+  if ((e = launch_pass<kEpiSplitT>(w->amap[0][0], w->amap[0][1], B[0], B[1], rows, w->sms, a, s)) != cudaSuccess) return e;
   a.out_hi = a.out_lo = nullptr;
   a.out_f32 = out;
   a.scale = inverse ? 1.f / (float)(m * m) : 1.f;
-  return launch_pass<kEpiF32T>(w->amap[1][0], w->amap[1][1], B[0], B[1], rows, a, s);
+  return launch_pass<kEpiF32T>(w->amap[1][0], w->amap[1][1], B[0], B[1], rows, w->sms, a, s);
 }
 
 cudaError_t tc_exit_waves(TcWork* w, const TcStepArgs& t, cudaStream_t s) {
@@ -662,7 +696,7 @@ cudaError_t tc_exit_waves(TcWork* w, const TcStepArgs& t, cudaStream_t s) {
   // a2, rows: psi -> (psi F)^T per tile
   a.out_hi = w->buf[1][0];
   a.out_lo = w->buf[1][1];
-  if ((e = launch_pass<kEpiSplitT>(w->amap[0][0], w->amap[0][1], F[0], F[1], rows, a, s)) != cudaSuccess) return e;
+  if ((e = launch_pass<kEpiSplitT>(w->amap[0][0], w->amap[0][1], F[0], F[1], rows, w->sms, a, s)) != cudaSuccess) return e;
   // a2, columns, and a3: Psi^T, modulus replaced, 1/m^2 folded in
   a.out_hi = w->buf[0][0];
   a.out_lo = w->buf[0][1];
@@ -670,7 +704,7 @@ cudaError_t tc_exit_waves(TcWork* w, const TcStepArgs& t, cudaStream_t s) {
   a.order = t.order;
   a.partial = t.partial;
   a.scale = 1.f / (float)(m * m);
-  if ((e = launch_pass<kEpiModulus>(w->amap[1][0], w->amap[1][1], F[0], F[1], rows, a, s)) != cudaSuccess) return e;
+  if ((e = launch_pass<kEpiModulus>(w->amap[1][0], w->amap[1][1], F[0], F[1], rows, w->sms, a, s)) != cudaSuccess) return e;
   // a4: inverse over the frequency rows (transposed back), then over the columns
   a.amp_t = nullptr;
   a.order = nullptr;
@@ -678,10 +712,10 @@ cudaError_t tc_exit_waves(TcWork* w, const TcStepArgs& t, cudaStream_t s) {
   a.scale = 1.f;
   a.out_hi = w->buf[1][0];
   a.out_lo = w->buf[1][1];
-  if ((e = launch_pass<kEpiSplitT>(w->amap[0][0], w->amap[0][1], G[0], G[1], rows, a, s)) != cudaSuccess) return e;
+  if ((e = launch_pass<kEpiSplitT>(w->amap[0][0], w->amap[0][1], G[0], G[1], rows, w->sms, a, s)) != cudaSuccess) return e;
   a.out_hi = a.out_lo = nullptr;
   a.out_f32 = t.R;
-  return launch_pass<kEpiF32>(w->amap[1][0], w->amap[1][1], G[0], G[1], rows, a, s);
+  return launch_pass<kEpiF32>(w->amap[1][0], w->amap[1][1], G[0], G[1], rows, w->sms, a, s);
 }
 
 cudaError_t launch_tc_amp(const float* d, float* amp_t, int m, int n_pos, cudaStream_t s) {
