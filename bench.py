@@ -169,6 +169,28 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest value of x over the ranks of the job (the slowest rank's time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def init_replicas(world: int, local: int) -> None:
+    """One process per GPU; the ranks share nothing but the timing reduction."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+
 def dist_init(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -259,10 +281,7 @@ def run_gpu(args, world, rank, local):
     import paper_2511_01793_gb300 as emg
 
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    init_replicas(world, local)
     emg.build()
     emg.load()
     w = synth.make_workload(WORKLOAD)
@@ -316,10 +335,7 @@ def run_gpu(args, world, rank, local):
         clk = clocks.stop()
         # per-kernel durations: the same K epochs as direct launches bracketed by events
         prof_ms, prof = timed_epochs(True)
-        if world > 1:
-            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, world)
         value = world * N * args.steps / (total_ms / 1e3)
         phi_end = emg.emg_misfit(ctx.ctx)
 
@@ -340,10 +356,7 @@ def run_gpu(args, world, rank, local):
                 t0 = time.perf_counter()
                 emg.emg_reconstruct_host(ctx.ctx, dn, zn, qn, 1, running=True)
                 t_e2e += time.perf_counter() - t0
-            if world > 1:
-                t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                t_e2e = float(t.item())
+            t_e2e = max_over_ranks(t_e2e, world)
             e2e = {"value": world * N * args.steps / t_e2e, "unit": UNIT,
                    "h2d_bytes_per_step": int(d.nbytes + zn.nbytes + qn.nbytes),
                    "d2h_bytes_per_step": int(zn.nbytes + qn.nbytes + 8)}
@@ -392,10 +405,7 @@ def run_gpu_grad(args, world, rank, local):
     import paper_2511_01793_gb300 as emg
 
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    init_replicas(world, local)
     emg.build()
     emg.load()
     w = synth.make_workload(args.workload)
@@ -463,6 +473,9 @@ def run_gpu_grad(args, world, rank, local):
             torch.cuda.synchronize()
             if i > 0:
                 t_e2e += time.perf_counter() - t0
+    total_ms = max_over_ranks(total_ms, world)
+    grad_only_ms = max_over_ranks(grad_only_ms, world)
+    t_e2e = max_over_ranks(t_e2e, world)
     value = world * N * args.steps / (total_ms / 1e3)
     alg = 28 * m * m          # patch read 8m^2 + amplitude 4m^2 + two gradient patches 16m^2
     achieved = alg * N / (grad_only_ms / 1e3) / 1e9
@@ -507,11 +520,11 @@ PREC_TARGET = os.path.join(ROOT, "tests", "golden", f"{PREC_WORKLOAD}_oracle_mis
 
 
 def read_prec_target():
-    """(epochs, Phi) of the FP64 oracle's last stored epoch, or (None, None)."""
+    """The FP64 oracle's misfit after each stored epoch, [(epoch, Phi), ...] (empty if absent)."""
     if not os.path.exists(PREC_TARGET):
-        return None, None
+        return []
     rows = [ln.split() for ln in open(PREC_TARGET) if ln.strip() and not ln.startswith("#")]
-    return int(rows[-1][0]), float(rows[-1][1])
+    return [(int(r[0]), float(r[1])) for r in rows]
 
 
 def run_gpu_prec(args, world, rank, local):
@@ -523,13 +536,15 @@ def run_gpu_prec(args, world, rank, local):
     import paper_2511_01793_gb300 as emg
 
     torch.cuda.set_device(local)
+    init_replicas(world, local)
     emg.build()
     emg.load()
     w = synth.make_workload(PREC_WORKLOAD)
     p = w.params
     n, m, N, B = p["n"], p["m"], len(w.pos), p["minibatch"]
     d = host_intensities(w, rank)
-    e_target, phi_target = read_prec_target()
+    oracle_phi = read_prec_target()
+    e_target, phi_target = oracle_phi[-1] if oracle_phi else (None, None)
     max_epochs = 3 * e_target if e_target else 0
     orders = synth.epoch_orders(N, max(max_epochs, args.warmup + args.steps + 2), p["order_seed"])
     stream = torch.cuda.Stream()
@@ -560,7 +575,7 @@ def run_gpu_prec(args, world, rank, local):
                 ev[i][1].record(stream)
             torch.cuda.synchronize()
             clk = clocks.stop()
-            ms = sum(a.elapsed_time(b) for a, b in ev)
+            ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
             counts = emg.emg_profile_read(ctx.ctx)
             # per-kind event times over two more epochs of direct launches
             emg.emg_set_profiling(ctx.ctx, True)
@@ -586,12 +601,17 @@ def run_gpu_prec(args, world, rank, local):
                     phi = emg.emg_misfit(ctx.ctx)
                     t_ms += a0.elapsed_time(a1)
                     phis.append(phi)
-                    if phi <= phi_target:
+                    if ttt is None and phi <= phi_target:
                         ttt = {"ms": round(t_ms, 3), "epochs": e + 1, "phi": phi}
+                    if ttt is not None and e + 1 >= e_target:
                         break
                 if ttt is None:
-                    ttt = {"ms": None, "epochs": None, "phi_after": phis}
-            res[name] = dict(value=N * args.steps / (ms / 1e3), ms_per_epoch=ms / args.steps, counts=counts,
+                    ttt = {"ms": None, "epochs": None}
+                # misfit per epoch against the oracle's on the same inputs, schedule and start
+                ttt["misfit_vs_oracle"] = [
+                    {"epoch": ep, "phi": phis[ep - 1], "oracle": po, "rel": round((phis[ep - 1] - po) / po, 6)}
+                    for ep, po in oracle_phi if ep <= len(phis)]
+            res[name] = dict(value=world * N * args.steps / (ms / 1e3), ms_per_epoch=ms / args.steps, counts=counts,
                              prof=prof, clocks=clk, ttt=ttt, ctx=ctx)
         # end to end on host buffers through the tensor-core variant
         ctx = res["bf16x3"]["ctx"]
@@ -607,6 +627,7 @@ def run_gpu_prec(args, world, rank, local):
             t0 = time.perf_counter()
             emg.emg_reconstruct_host(ctx.ctx, dn, zn, qn, 1, running=True)
             t_e2e += time.perf_counter() - t0
+    t_e2e = max_over_ranks(t_e2e, world)
     tc = res["bf16x3"]
     dft_ms, dft_launches = tc["prof"]["dft"]
     # executed MMA work of the four GEMM passes: 2 (b m) (2m) (2m) flops per pass and product, 3 products
@@ -617,7 +638,7 @@ def run_gpu_prec(args, world, rank, local):
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
     line = {
         "metric": "scan positions/sec per eMAGPIE epoch (DFT pair on tensor cores, BF16 x3 split)",
-        "value": tc["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "value": tc["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tc["ms_per_epoch"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16x3/f32", "data": "synthetic",
         "config": {"workload": f"{PREC_WORKLOAD}: object {n}^2, probe {m}^2, {N} positions (64x64 raster, step 28, "
@@ -626,7 +647,7 @@ def run_gpu_prec(args, world, rank, local):
         "fft32": {"value": res["fft32"]["value"], "ms_per_epoch": res["fft32"]["ms_per_epoch"]},
         "time_to_oracle_misfit": {"target": {"epochs": e_target, "phi": phi_target},
                                   "bf16x3": tc["ttt"], "fft32": res["fft32"]["ttt"]},
-        "e2e": {"value": N * args.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(dn.nbytes + zn.nbytes +
+        "e2e": {"value": world * N * args.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(dn.nbytes + zn.nbytes +
                                                                                           qn.nbytes),
                 "d2h_bytes_per_step": int(zn.nbytes + qn.nbytes + 8)},
         "gpu_launches": sum(v[1] for v in tc["counts"].values()),
@@ -638,7 +659,11 @@ def run_gpu_prec(args, world, rank, local):
                                f"({dft_ms / 2:.3f} ms/epoch of {tc['ms_per_epoch']:.3f})"},
         "clocks": tc["clocks"],
     }
-    if not args.no_cpu_baseline:
+    if rank != 0:
+        for r in res.values():
+            r["ctx"].close()
+        return
+    if world == 1 and not args.no_cpu_baseline:
         rate, done, dt = cpu_oracle_sample(w, d, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{done} positions from the initial state, {dt:.1f} s single-thread FP64"}
@@ -671,6 +696,7 @@ def run_gpu_batch(args, world, rank, local):
     import paper_2511_01793_gb300 as emg
 
     torch.cuda.set_device(local)
+    init_replicas(world, local)
     emg.build()
     emg.load()
     probs = batch_problems()
@@ -721,15 +747,15 @@ def run_gpu_batch(args, world, rank, local):
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         clk = clocks.stop()
-        total_ms = sum(a.elapsed_time(b) for a, b in ev)
+        total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
         launches = sum(sum(v[1] for v in emg.emg_profile_read(c.ctx).values()) for c in ctxs)
         emg.emg_batch_destroy(batch)
-    value = total_pos * args.steps / (total_ms / 1e3)
+    value = world * total_pos * args.steps / (total_ms / 1e3)
     achieved = alg_bytes * args.steps / (total_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     line = {
         "metric": "scan positions/sec per epoch over a batch of reconstructions", "value": value, "unit": UNIT,
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batch64: {len(probs)} problems, {total_pos} positions per epoch, object "
                                "256-1024, probe 64-256, 2-3 levels, one graph launch per epoch",
@@ -741,7 +767,8 @@ def run_gpu_batch(args, world, rank, local):
                      "kernel": "whole epoch graph (algorithmic bytes of all positions / epoch time)"},
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()
 

@@ -149,3 +149,42 @@ def test_tc_epochs_are_bitwise_repeatable(lib, torch):
         ctx.close()
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
     assert np.array_equal(res[0][2][1], res[1][2][1])
+
+
+def test_full_size_precision_minibatch_matches_the_oracle(lib, torch):
+    """One minibatch of the precision workload at full size (object 2048^2,
+    probe 256^2, B = 256, L = 3 bilinear) in the launch configuration the bench
+    times, with both DFT variants, against the oracle on every covered pixel.
+    Only the minibatch's positions carry data (the step reads no other)."""
+    import synth
+    from emg_cases import c64, gpu_params
+
+    w = synth.make_workload("prec_n2048_m256")
+    p = w.params
+    n, m, B = p["n"], p["m"], p["minibatch"]
+    rng = np.random.Generator(np.random.PCG64(77))
+    idx = [int(k) for k in synth.epoch_orders(len(w.pos), 1, p["order_seed"])[0][:B]]
+    d = np.zeros((len(w.pos), m, m), dtype=np.float32)
+    d_mb = O.forward_intensity(w.q_true, w.z_true, w.pos[idx])
+    d[idx] = synth.poisson_noise(d_mb, p["peak"], rng).astype(np.float32)
+    z0 = c64(synth.perturb(w.z_true, 0.3, rng))
+    q0 = c64(synth.perturb(w.q_true, 0.3, rng))
+    po = oracle_params(alpha=p["alpha"], levels=p["levels"], minibatch=B, prolong=p["prolong"])
+    a64 = np.sqrt(np.maximum(d.astype(np.float64), 0.0))
+    oq = O.Params(alpha=float(np.float32(po.alpha)), levels=po.levels, minibatch=B, prolong=po.prolong,
+                  combine=po.combine, w_eps=float(np.float32(po.w_eps)), joint=po.joint)
+    z_o, q_o = O.minibatch_step(z0.astype(np.complex128), q0.astype(np.complex128), w.pos, a64, idx, oq)
+    mask = np.zeros((n, n), dtype=bool)
+    for k in idx:
+        r0, c0 = w.pos[k]
+        mask[max(r0, 0):min(r0 + m, n), max(c0, 0):min(c0 + m, n)] = True
+    for dft, tol in ((lib.EMG_DFT_FFT32, 1e-5), (lib.EMG_DFT_BF16X3, TC_STEP_TOL)):
+        ctx = lib.Context(w.pos, d, n, n, gpu_params(lib, po, dft=dft), obj=torch.from_numpy(z0),
+                          probe=torch.from_numpy(q0))
+        lib.emg_step_minibatch(ctx.ctx, idx)
+        z_g, q_g = state(ctx)
+        ctx.close()
+        e_z, e_q = rel_err(z_g, z_o, mask), rel_err(q_g, q_o)
+        print(f"dft={dft}: object {e_z:.2e} probe {e_q:.2e}")
+        assert e_z <= tol and e_q <= tol
+        assert np.array_equal(z_g[~mask], z0.astype(np.complex128)[~mask])
