@@ -12,11 +12,12 @@
 // other axis), replace the modulus (a3) or store FP32.
 //
 // Persistent kernel, one CTA per SM, looping over 128 x 256 output tiles.  Warp
-// 0 streams A and B chunks of 64 bf16 along K through a two-stage shared-memory
-// ring with TMA (128-byte swizzle); warp 1 owns all 512 columns of tensor memory
+// 0 streams A and B chunks of 32 bf16 along K through a four-stage shared-memory
+// ring with TMA (64-byte swizzle); warp 1 owns all 512 columns of tensor memory
 // as two 256-column accumulators and issues tcgen05.mma from one lane; warps
-// 2-5 drain an accumulator with tcgen05.ld and run the epilogue while the MMAs
-// of the next tile fill the other one.  Every mbarrier wait is bounded in
+// 2-9 drain an accumulator with tcgen05.ld (two warps per lane quadrant, each
+// half of the columns) and run the epilogue while the MMAs of the next tile
+// fill the other accumulator.  Every mbarrier wait is bounded in
 // time: on expiry the kernel records an error flag, waits (bounded) for what it
 // issued, frees its tensor memory and returns.
 #include <cuda.h>
@@ -36,13 +37,15 @@ namespace {
 
 constexpr int kBM = 128;                            // accumulator rows = TMEM lanes
 constexpr int kBN = 256;                            // accumulator columns (FP32)
-constexpr int kBK = 64;                             // bf16 per 128-byte swizzled row
-constexpr int kStages = 2;
-constexpr int kTileA = kBM * kBK * 2;               // 16 KB
-constexpr int kTileB = kBN * kBK * 2;               // 32 KB
+constexpr int kBK = 32;                             // bf16 per 64-byte swizzled row
+constexpr int kStages = 4;
+constexpr int kSwizzleBytes = kBK * 2;              // one swizzle atom row
+constexpr int kTileA = kBM * kBK * 2;               // 8 KB
+constexpr int kTileB = kBN * kBK * 2;               // 16 KB
 constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;  // A hi, A lo, B hi, B lo
 constexpr int kTcSmem = kStages * kStageBytes + 1024;  // + alignment slack
-constexpr int kTcThreads = 192;
+constexpr int kEpiWarps = 8;                        // two per TMEM lane quadrant, each half the columns
+constexpr int kTcThreads = 32 * (2 + kEpiWarps);
 constexpr uint32_t kTmemCols = 2 * kBN;             // two accumulators
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per wait
 
@@ -106,17 +109,17 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzling:
+// Shared-memory matrix descriptor of a K-major tile with 64-byte swizzling:
 // start address >> 4 (bits 0-13), leading byte offset (unused for this layout,
-// bits 16-29), stride byte offset 1024 B = 8 rows x 128 B (bits 32-45), the
+// bits 16-29), stride byte offset 512 B = 8 rows x 64 B (bits 32-45), the
 // descriptor version 1 (bits 46-48), base offset 0 (tiles are 1024-byte
-// aligned), swizzle mode 2 = 128 B (bits 61-63).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// aligned), swizzle mode 4 = 64 B (bits 61-63).
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)((8 * kSwizzleBytes) >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)4 << 61;
   return d;
 }
 
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ __align__(8) uint64_t full_bar[kStages];   // stage loaded (TMA bytes arrived)
   __shared__ __align__(8) uint64_t empty_bar[kStages];  // stage consumed by the MMAs
   __shared__ __align__(8) uint64_t accf_bar[2];         // accumulator complete
-  __shared__ __align__(8) uint64_t acce_bar[2];         // accumulator drained by the 4 epilogue warps
+  __shared__ __align__(8) uint64_t acce_bar[2];         // accumulator drained by the epilogue warps
   __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_sh;
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf_bar[b], 1);
-      mbar_init(&acce_bar[b], 4);
+      mbar_init(&acce_bar[b], kEpiWarps);
     }
     mbar_init(&drain_bar, 1);
     abort_sh = 0;
@@ -277,10 +280,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const uint32_t st = tiles_s + s * kStageBytes;
 #pragma unroll
           for (int kk = 0; kk < kBK / 16; ++kk) {
-            const uint64_t ah = sw128_desc(st + kk * 32);
-            const uint64_t al = sw128_desc(st + kTileA + kk * 32);
-            const uint64_t bh = sw128_desc(st + 2 * kTileA + kk * 32);
-            const uint64_t bl = sw128_desc(st + 2 * kTileA + kTileB + kk * 32);
+            const uint64_t ah = sw_desc(st + kk * 32);
+            const uint64_t al = sw_desc(st + kTileA + kk * 32);
+            const uint64_t bh = sw_desc(st + 2 * kTileA + kk * 32);
+            const uint64_t bl = sw_desc(st + 2 * kTileA + kTileB + kk * 32);
             umma_bf16(d, ah, bh, (kc | kk) != 0);
             umma_bf16(d, ah, bl, 1);
             umma_bf16(d, al, bh, 1);
@@ -298,7 +301,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
   } else {
-    const int q = warp & 3;  // this warp may access TMEM lanes 32 q .. 32 q + 31
+    const int q = warp & 3;              // this warp may access TMEM lanes 32 q .. 32 q + 31
+    const int ew = warp - 2;             // epilogue warp 0 .. 7
+    const int c_lo = (ew >> 2) * (kBN / 2);  // its half of the accumulator columns
     const int m = a.m;
     int local = 0;
     for (int t = blockIdx.x; t < a.tiles; t += gridDim.x, ++local) {
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const uint32_t tb = tmem + (uint32_t)(buf * kBN) + ((uint32_t)(q * 32) << 16);
       float acc = 0.f;
 #pragma unroll 1
-      for (int c0 = 0; c0 < kBN; c0 += 32) {
+      for (int c0 = c_lo; c0 < c_lo + kBN / 2; c0 += 32) {
         float v[32];
         __syncwarp();
         tmem_ld32(tb + (uint32_t)c0, v);
@@ -381,7 +386,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             a.out_f32[((size_t)kb * m + u0 + j) * m + r] = make_float2(v[2 * j] * a.scale, v[2 * j + 1] * a.scale);
         }
       }
-      // the accumulator is free for the tile after next once all four warps have read it
+      // the accumulator is free for the tile after next once every epilogue warp has read it
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce_bar[buf]);
@@ -389,7 +394,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         double dsum = (double)acc;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, off);
-        if (lane == 0) a.partial[(size_t)t * 4 + q] = dsum;
+        if (lane == 0) a.partial[(size_t)t * kEpiWarps + ew] = dsum;
       }
     }
   }
@@ -471,7 +476,7 @@ cudaError_t get_encoder(EncodeTiledFn* out) {
   return cudaSuccess;
 }
 
-// 2-D bf16 tensor of `rows` rows of `inner` elements, boxes of 64 x box_rows, 128-byte swizzle.
+// 2-D bf16 tensor of `rows` rows of `inner` elements, boxes of kBK x box_rows, 64-byte swizzle.
 cudaError_t make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t rows, uint32_t box_rows) {
   EncodeTiledFn enc = nullptr;
   cudaError_t e = get_encoder(&enc);
@@ -481,7 +486,7 @@ cudaError_t make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_
   const cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
   const cuuint32_t es[2] = {1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -656,7 +661,7 @@ void tc_work_destroy(TcWork* w) {
 
 int* tc_error_flag(TcWork* w) { return w->d_err; }
 
-int tc_tiles_per_position(int m) { return (m / kBM) * (2 * m / kBN) * 4; }  // x 4 epilogue warps
+int tc_tiles_per_position(int m) { return (m / kBM) * (2 * m / kBN) * kEpiWarps; }  // per epilogue warp
 
 cudaError_t tc_dft2(TcWork* w, const float2* in, float2* out, int count, int inverse, cudaStream_t s) {
   if (count < 1 || count > w->cap) return cudaErrorInvalidValue;
