@@ -11,9 +11,11 @@
 // and can write them transposed per tile (the next pass then transforms the
 // other axis), replace the modulus (a3) or store FP32.
 //
-// Persistent kernel, one CTA per SM, looping over 128 x 256 output tiles.  Warp
-// 0 streams A and B chunks of 32 bf16 along K through a four-stage shared-memory
-// ring with TMA (64-byte swizzle); warp 1 owns all 512 columns of tensor memory
+// Persistent kernel, one CTA per SM, in clusters of two CTAs that take the two
+// 128-row halves of a 256 x 256 output block: each CTA loads its own A rows and
+// half of the block's B (the DFT matrix) with a TMA multicast into both CTAs,
+// so B crosses L2 once per pair.  Warp 0 streams A and B chunks of 32 bf16
+// along K through a four-stage shared-memory ring with TMA (64-byte swizzle); warp 1 owns all 512 columns of tensor memory
 // as two 256-column accumulators and issues tcgen05.mma from one lane; warps
 // 2-9 drain an accumulator with tcgen05.ld (two warps per lane quadrant, each
 // half of the columns) and run the epilogue while the MMAs of the next tile
@@ -106,6 +108,23 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// The same load with cluster multicast: the box lands at the same shared-memory
+// offset in every CTA of `mask` and completes bytes on the mbarrier at the same
+// offset in each of them.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -134,6 +153,14 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint6
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// Arrives (when the MMAs issued so far complete) on the mbarrier at this
+// offset in every CTA of `mask`.
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
+                   "r"(smem_u32(bar)), "h"(mask)
                : "memory");
 }
 
@@ -166,7 +193,7 @@ __device__ __forceinline__ void split_pair(float re, float im, uint32_t& hi, uin
 
 struct TcPassArgs {
   int m;                    // transform size; K = 2m, each tile has m rows
-  int tiles_n, tiles;       // output tiles along N, and in all
+  int tiles_n, m_tiles;     // output tiles along N and along M
   uint32_t* out_hi;         // split outputs, bf16 pairs [rows][m]
   uint32_t* out_lo;
   float2* out_f32;          // FP32 outputs [rows][m]
@@ -191,7 +218,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
              const TcPassArgs a) {
   extern __shared__ uint8_t tc_smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kStages];   // stage loaded (TMA bytes arrived)
-  __shared__ __align__(8) uint64_t empty_bar[kStages];  // stage consumed by the MMAs
+  __shared__ __align__(8) uint64_t empty_bar[kStages];  // stage consumed by the MMAs of both CTAs
   __shared__ __align__(8) uint64_t accf_bar[2];         // accumulator complete
   __shared__ __align__(8) uint64_t acce_bar[2];         // accumulator drained by the epilogue warps
   __shared__ __align__(8) uint64_t drain_bar;
@@ -207,7 +234,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
+      mbar_init(&empty_bar[s], 2);
     }
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
@@ -227,15 +254,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
-  __syncthreads();
+  cluster_sync_all();  // both CTAs' barriers exist before either multicasts into the other
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
+  const int rank = (int)(blockIdx.x & 1), n_cl = (int)(gridDim.x >> 1), cl_id = (int)(blockIdx.x >> 1);
+  const int pairs = ((a.m_tiles + 1) >> 1) * a.tiles_n;
+  constexpr uint16_t kBoth = 3;
 
   if (warp == 0) {
     if (lane == 0) {
       uint32_t it = 0;  // chunks issued so far (the ring position runs on across tiles)
-      for (int t = blockIdx.x; t < a.tiles && !abort_sh; t += gridDim.x) {
-        const int m_tile = t / a.tiles_n, n_tile = t % a.tiles_n;
+      for (int pr = cl_id; pr < pairs && !abort_sh; pr += n_cl) {
+        const int m_tile = 2 * (pr / a.tiles_n) + rank, n_tile = pr % a.tiles_n;
         for (int kc = 0; kc < KC; ++kc, ++it) {
           const uint32_t s = it % kStages;
           if (it >= kStages && !mbar_wait(&empty_bar[s], ((it / kStages) + 1) & 1, &abort_sh)) {
@@ -247,8 +277,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           mbar_expect_tx(&full_bar[s], kStageBytes);
           tma_load_2d(st, &mAh, &full_bar[s], kc * kBK, m_tile * kBM);
           tma_load_2d(st + kTileA, &mAl, &full_bar[s], kc * kBK, m_tile * kBM);
-          tma_load_2d(st + 2 * kTileA, &mBh, &full_bar[s], kc * kBK, n_tile * kBN);
-          tma_load_2d(st + 2 * kTileA + kTileB, &mBl, &full_bar[s], kc * kBK, n_tile * kBN);
+          // my half of the block's B rows, into both CTAs
+          const uint32_t bo = (uint32_t)rank * (kTileB / 2);
+          tma_load_2d_mc(st + 2 * kTileA + bo, &mBh, &full_bar[s], kc * kBK, n_tile * kBN + rank * (kBN / 2), kBoth);
+          tma_load_2d_mc(st + 2 * kTileA + kTileB + bo, &mBl, &full_bar[s], kc * kBK,
+                         n_tile * kBN + rank * (kBN / 2), kBoth);
         }
       }
       if (abort_sh) {  // let the copies already issued land before the CTA exits
@@ -262,7 +295,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       bool ok = true;
       uint32_t it = 0;
       int local = 0;
-      for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x, ++local) {
+      for (int pr = cl_id; pr < pairs && ok; pr += n_cl, ++local) {
         const int buf = local & 1;
         if (local >= 2 && !mbar_wait(&acce_bar[buf], ((local >> 1) + 1) & 1, &abort_sh)) {
           ok = false;
@@ -288,7 +321,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             umma_bf16(d, ah, bl, 1);
             umma_bf16(d, al, bh, 1);
           }
-          umma_commit(&empty_bar[s]);
+          umma_commit_mc(&empty_bar[s], kBoth);  // the stage holds B rows that both CTAs load
         }
         if (ok) umma_commit(&accf_bar[buf]);
       }
@@ -306,7 +339,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int c_lo = (ew >> 2) * (kBN / 2);  // its half of the accumulator columns
     const int m = a.m;
     int local = 0;
-    for (int t = blockIdx.x; t < a.tiles; t += gridDim.x, ++local) {
+    for (int pr = cl_id; pr < pairs; pr += n_cl, ++local) {
       const int buf = local & 1;
       const bool got = mbar_wait(&accf_bar[buf], (local >> 1) & 1, &abort_sh);
       if (!__all_sync(0xffffffffu, got)) {
@@ -317,7 +350,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         break;
       }
       tc_fence_after();
-      const int m_tile = t / a.tiles_n, n_tile = t % a.tiles_n;
+      const int m_tile = 2 * (pr / a.tiles_n) + rank, n_tile = pr % a.tiles_n;
+      const int t = m_tile * a.tiles_n + n_tile;
+      const bool real = m_tile < a.m_tiles;  // the second half of the last block may lie past the rows
       const int gr = m_tile * kBM + q * 32 + lane;  // global row
       const int kb = gr / m, r = gr % m;
       const uint32_t tb = tmem + (uint32_t)(buf * kBN) + ((uint32_t)(q * 32) << 16);
@@ -327,6 +362,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         float v[32];
         __syncwarp();
         tmem_ld32(tb + (uint32_t)c0, v);
+        if (!real) continue;
         const int u0 = (n_tile * kBN + c0) >> 1;  // first complex column of the chunk
         if constexpr (EPI == kEpiSplitT) {
 #pragma unroll
@@ -394,7 +430,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         double dsum = (double)acc;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, off);
-        if (lane == 0) a.partial[(size_t)t * kEpiWarps + ew] = dsum;
+        if (lane == 0 && real) a.partial[(size_t)t * kEpiWarps + ew] = dsum;
       }
     }
   }
@@ -405,6 +441,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
+  cluster_sync_all();  // no CTA leaves while its partner may still multicast into it
 }
 
 // Complex64 tiles -> high / low bf16 pairs (same order).
@@ -558,7 +595,7 @@ cudaError_t get_tables(int m, const TcTables** out) {
   if (e == cudaSuccess) e = cudaMemcpy(d, h, 4 * per * sizeof(uint16_t), cudaMemcpyHostToDevice);
   free(h);
   TcTables nt;
-  for (int j = 0; e == cudaSuccess && j < 4; ++j) e = make_map(&nt.map[j], d + j * per, K, K, kBN);
+  for (int j = 0; e == cudaSuccess && j < 4; ++j) e = make_map(&nt.map[j], d + j * per, K, K, kBN / 2);
   if (e != cudaSuccess) {
     if (d) cudaFree(d);
     return e;
@@ -578,10 +615,23 @@ template <int EPI>
 cudaError_t launch_pass(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
                         int rows, int sms, TcPassArgs a, cudaStream_t s) {
   a.tiles_n = 2 * a.m / kBN;
-  a.tiles = a.tiles_n * (rows / kBM);
-  const int grid = a.tiles < sms ? a.tiles : sms;
-  k_tc_dft<EPI><<<grid, kTcThreads, kTcSmem, s>>>(ah, al, bh, bl, a);
-  return cudaGetLastError();
+  a.m_tiles = rows / kBM;
+  const int pairs = ((a.m_tiles + 1) / 2) * a.tiles_n;
+  const int clusters = pairs < sms / 2 ? pairs : sms / 2;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * clusters);
+  cfg.blockDim = dim3(kTcThreads);
+  cfg.dynamicSmemBytes = kTcSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_dft<EPI>, ah, al, bh, bl, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t set_tc_attrs() {
