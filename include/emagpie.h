@@ -212,6 +212,31 @@ emg_status emg_misfit(emg_ctx* ctx, double* out);
 emg_status emg_set_epoch(emg_ctx* ctx, int64_t epoch);
 
 /*
+ * Host-only: the stopping criterion of Sec. 4.1 and the noise-floor rule of
+ * Sec. 4.3 applied to residuals r[0..n-1] (r[t-1] = Phi after outer iteration
+ * t).  For t >= window the moving average of the last `window` residuals is
+ * formed; a check counts when that average is not below the best of the
+ * earlier averages (an improvement resets the count), and the run stops at the
+ * first t at which the count reaches `patience`.  With floor > 0 (Phi at the
+ * true object and probe on the noisy data) it also stops at the first t with
+ * r_t < 0.9 floor.  *out receives that t (1-based), or 0 if the run does not
+ * stop within the n residuals.  EMG_EINVAL for n < 0, window or patience < 1,
+ * a negative or non-finite floor, or a NULL pointer that is needed.
+ */
+emg_status emg_stopping_epoch(const double* r, int32_t n, int32_t window, int32_t patience, double floor,
+                              int32_t* out);
+
+/*
+ * Runs epochs (default schedule) one at a time, evaluating Phi after each as
+ * emg_misfit does, until the rules of emg_stopping_epoch stop the run or
+ * max_epochs have run.  epochs_run (host) receives the number of epochs;
+ * misfit (host [max_epochs], or NULL) the residual after each.  Synchronises
+ * once per epoch.
+ */
+emg_status emg_run_until(emg_ctx* ctx, int32_t max_epochs, int32_t window, int32_t patience, double floor,
+                         int32_t* epochs_run, double* misfit);
+
+/*
  * Host-only: the default schedule's permutation of 0..n-1 for one epoch.
  * SplitMix64 (Steele, Lea, Flood 2014) seeded with
  * seed + epoch * 0x9E3779B97F4A7C15 (mod 2^64), then Fisher-Yates from

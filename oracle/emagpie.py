@@ -34,6 +34,9 @@ notes of the repository):
   < 0; at exactly 0 the principal root is kept (Eq. geomean allows both).
 * A patch with max|z_k|^2 = 0 leaves the probe unchanged and is excluded from
   the probe mean.
+* Stopping criterion (Sec. 4.1): as printed, the best average includes the
+  current one, so "average >= best" would always hold; the best is read as the
+  minimum of the earlier averages.
 """
 from __future__ import annotations
 
@@ -50,7 +53,7 @@ __all__ = [
     "joint_step", "minibatch_step", "run_epochs", "sequential_sweep",
     "forward_intensity", "dp_avg", "dp_avg_scale", "splitmix64_stream",
     "schedule_permutation", "magnitude_error", "illuminated_region",
-    "aligned_errors", "misfit_gradients",
+    "aligned_errors", "misfit_gradients", "stopping_epoch",
 ]
 
 
@@ -466,6 +469,35 @@ def aligned_errors(z, Q, z_ref, Q_ref, region) -> dict:
     phase = np.angle(c * zr * np.conj(zrefr))
     prb = float(np.linalg.norm(Q / c - Q_ref) / np.linalg.norm(Q_ref))
     return dict(c=c, object=obj, probe=prb, phase_rms=float(np.sqrt(np.mean(phase ** 2))))
+
+
+def stopping_epoch(r: Sequence[float], window: int = 5, patience: int = 10, floor: float = 0.0) -> int:
+    """The outer iteration (1-based) at which the run of Sec. 4.1 stops, or 0.
+
+    r[t-1] is the residual r_t = Phi(Q^(t), z^(t)) after iteration t.  For
+    t >= window the moving average rbar_t = (1/window) sum_{i<window} r_{t-i}
+    is formed.  A check at t counts when rbar_t is not below the best of the
+    earlier averages; any improvement resets the count.  The run stops at the
+    first t at which the count reaches `patience`.  With floor > 0 (the noise
+    residual of Sec. 4.3: Phi at the true object and probe on the noisy data),
+    it also stops at the first t with r_t < 0.9 floor.
+    """
+    best = None
+    count = 0
+    for t in range(1, len(r) + 1):
+        if floor > 0.0 and r[t - 1] < 0.9 * floor:
+            return t
+        if t < window:
+            continue
+        avg = sum(r[t - 1 - i] for i in range(window)) / window
+        if best is not None and avg >= best:
+            count += 1
+            if count >= patience:
+                return t
+        else:
+            count = 0
+            best = avg
+    return 0
 
 
 # ---------------------------------------------------------------------------

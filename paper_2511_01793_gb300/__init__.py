@@ -25,7 +25,7 @@ __all__ = [
     "build", "load", "lib_path", "exported_symbols", "emg_default_params", "emg_status_string",
     "emg_create", "emg_set_intensity", "emg_bind_state", "emg_normalize_probe",
     "emg_step_minibatch", "emg_position_stats", "emg_set_verify", "emg_run_epochs", "emg_misfit",
-    "emg_set_epoch", "emg_schedule_permutation", "emg_reconstruct_host",
+    "emg_set_epoch", "emg_schedule_permutation", "emg_stopping_epoch", "emg_run_until", "emg_reconstruct_host",
     "emg_simulate_intensity", "emg_fft2", "emg_dft2_bf16x3", "emg_step_minibatch_noalloc", "emg_misfit_gradient",
     "emg_set_cluster", "emg_autotune", "emg_batch_create", "emg_batch_run_epochs", "emg_batch_destroy",
     "emg_set_profiling",
@@ -85,6 +85,10 @@ _SIGS = {
     "emg_simulate_intensity": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_int32,
                                               _VP, ctypes.c_int32, _VP, _VP]),
     "emg_fft2": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP]),
+    "emg_stopping_epoch": (ctypes.c_int, [_F64P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                          ctypes.POINTER(ctypes.c_int32)]),
+    "emg_run_until": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_int32), _F64P]),
     "emg_dft2_bf16x3": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP]),
     "emg_step_minibatch_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_int32,
                                                   _VP, _VP, ctypes.c_int32, _I32P, ctypes.c_int32,
@@ -261,6 +265,24 @@ def emg_simulate_intensity(object_ptr: int, n_rows: int, n_cols: int, probe_ptr:
                            pos_ptr: int, n_pos: int, out_ptr: int, stream: int = 0) -> None:
     _check(load().emg_simulate_intensity(object_ptr, n_rows, n_cols, probe_ptr, m, pos_ptr, n_pos,
                                          out_ptr, _VP(stream)), "emg_simulate_intensity")
+
+
+def emg_stopping_epoch(r, window: int = 5, patience: int = 10, floor: float = 0.0) -> int:
+    """The outer iteration (1-based) at which the run stops, or 0 (Sec. 4.1, 4.3)."""
+    a = np.ascontiguousarray(r, dtype=np.float64)
+    out = ctypes.c_int32()
+    _check(load().emg_stopping_epoch(a.ctypes.data_as(_F64P), len(a), window, patience, floor, ctypes.byref(out)),
+           "emg_stopping_epoch")
+    return int(out.value)
+
+
+def emg_run_until(ctx: int, max_epochs: int, window: int = 5, patience: int = 10, floor: float = 0.0):
+    """Runs epochs until the stopping rules fire; returns the residual after each epoch."""
+    hist = np.zeros(max(max_epochs, 1), dtype=np.float64)
+    n = ctypes.c_int32()
+    _check(load().emg_run_until(ctx, max_epochs, window, patience, floor, ctypes.byref(n),
+                                hist.ctypes.data_as(_F64P)), "emg_run_until", ctx)
+    return hist[:n.value].copy()
 
 
 def emg_fft2(in_ptr: int, out_ptr: int, m: int, count: int, inverse: bool, stream: int = 0) -> None:

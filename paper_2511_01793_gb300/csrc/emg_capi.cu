@@ -572,6 +572,28 @@ bool is_device_pointer(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Stopping criterion of Sec. 4.1 with the noise-floor rule of Sec. 4.3 (see the header).
+int32_t stopping_epoch(const double* r, int n, int window, int patience, double floor) {
+  double best = 0.0;
+  bool have_best = false;
+  int count = 0;
+  for (int t = 1; t <= n; ++t) {
+    if (floor > 0.0 && r[t - 1] < 0.9 * floor) return t;
+    if (t < window) continue;
+    double sum = 0.0;
+    for (int i = 0; i < window; ++i) sum += r[t - 1 - i];
+    const double avg = sum / window;
+    if (have_best && avg >= best) {
+      if (++count >= patience) return t;
+    } else {
+      count = 0;
+      best = avg;
+      have_best = true;
+    }
+  }
+  return 0;
+}
+
 emg_status set_intensity_impl(emg_ctx* c, const float* intensity) {
   const size_t n = (size_t)c->n_pos * c->m * c->m;
   const float* src = intensity;
@@ -789,6 +811,36 @@ emg_status emg_set_epoch(emg_ctx* c, int64_t epoch) {
   if (!c) return EMG_EINVAL;
   if (epoch < 0) return fail(c, EMG_EINVAL, "epoch < 0");
   c->epoch = epoch;
+  return EMG_OK;
+}
+
+emg_status emg_stopping_epoch(const double* r, int32_t n, int32_t window, int32_t patience, double floor,
+                              int32_t* out) {
+  if (!out || n < 0 || (n > 0 && !r) || window < 1 || patience < 1 || !(floor >= 0.0) || !isfinite(floor))
+    return EMG_EINVAL;
+  *out = stopping_epoch(r, n, window, patience, floor);
+  return EMG_OK;
+}
+
+emg_status emg_run_until(emg_ctx* c, int32_t max_epochs, int32_t window, int32_t patience, double floor,
+                         int32_t* epochs_run, double* misfit) {
+  if (!c) return EMG_EINVAL;
+  emg_status st = check_bound(c);
+  if (st != EMG_OK) return st;
+  if (!epochs_run || max_epochs < 0 || window < 1 || patience < 1 || !(floor >= 0.0) || !isfinite(floor))
+    return fail(c, EMG_EINVAL, "invalid stopping parameters");
+  DeviceGuard g(c->device);
+  std::vector<double> r;
+  r.reserve((size_t)max_epochs);
+  *epochs_run = 0;
+  for (int32_t e = 0; e < max_epochs; ++e) {
+    double phi = 0.0;
+    if ((st = run_epochs_impl(c, 1, nullptr, nullptr, &phi)) != EMG_OK) return st;
+    r.push_back(phi);
+    if (misfit) misfit[e] = phi;
+    *epochs_run = e + 1;
+    if (stopping_epoch(r.data(), (int)r.size(), window, patience, floor) != 0) break;
+  }
   return EMG_OK;
 }
 

@@ -17,6 +17,7 @@ from .inputs import (  # noqa: F401
     make_probe,
     make_scan,
     blur_probe,
+    aberrate_probe,
     poisson_noise,
     noise_percent,
     epoch_orders,

@@ -131,6 +131,27 @@ def blur_probe(q: np.ndarray, sigma: float = 2.0) -> np.ndarray:
     return np.fft.ifft2(np.fft.fft2(q) * transfer)
 
 
+def aberrate_probe(q: np.ndarray, rng: np.random.Generator, sigma: float = 2.0, ramp: float = 7.0,
+                   defocus: float = 0.6, astigmatism: float = 0.2, noise: float = 0.01) -> np.ndarray:
+    """The paper's aberrated initial probe (Sec. 4.1, probe initialisation):
+    the magnitude of q blurred in Fourier space (sigma px), times
+    exp(i [a_x x + a_y y + defocus (x^2 + y^2) + astigmatism (x^2 - y^2)]),
+    plus complex Gaussian noise of `noise` times the largest magnitude.
+    x, y run over [-1, 1] across the probe; (a_x, a_y) has a uniformly drawn
+    direction and length ramp / 2, so that the linear phase changes by `ramp`
+    radians across the field of view along it.
+    """
+    m0, m1 = q.shape
+    amp = np.abs(blur_probe(np.abs(q).astype(np.complex128), sigma))
+    y, x = np.meshgrid(np.linspace(-1.0, 1.0, m0), np.linspace(-1.0, 1.0, m1), indexing="ij")
+    theta = rng.uniform(0.0, 2.0 * math.pi)
+    ax, ay = 0.5 * ramp * math.cos(theta), 0.5 * ramp * math.sin(theta)
+    phase = ax * x + ay * y + defocus * (x ** 2 + y ** 2) + astigmatism * (x ** 2 - y ** 2)
+    q0 = amp * np.exp(1j * phase)
+    scale = noise * float(amp.max()) / math.sqrt(2.0)
+    return q0 + scale * (rng.standard_normal(q.shape) + 1j * rng.standard_normal(q.shape))
+
+
 def poisson_noise(d_clean: np.ndarray, peak: float,
                   rng: np.random.Generator) -> np.ndarray:
     """Poisson counts at ``peak`` photons for the mean per-pattern maximum.

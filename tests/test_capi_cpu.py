@@ -110,3 +110,24 @@ def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
     monkeypatch.setattr(emg._build, "OUT_DIR", str(tmp_path))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         emg.load()
+
+
+def test_stopping_rule_matches_the_oracle(lib):
+    """Host-only stopping criterion (Sec. 4.1) and noise-floor rule (Sec. 4.3)."""
+    rng = np.random.default_rng(5)
+    for trial in range(300):
+        n = int(rng.integers(0, 60))
+        # a decaying residual with noise and plateaus, as a run produces
+        r = np.maximum(1.0 + 10.0 * np.exp(-rng.uniform(0.02, 0.5) * np.arange(n))
+                       + rng.normal(0, rng.choice([0.0, 0.01, 0.2]), n), 0.1)
+        if trial % 3 == 0:
+            r = np.round(r, 1)  # exact ties between averages
+        w, p = int(rng.integers(1, 8)), int(rng.integers(1, 12))
+        floor = float(rng.choice([0.0, 1.0, 1.2, 2.0]))
+        assert emg.emg_stopping_epoch(r, w, p, floor) == O.stopping_epoch(list(r), w, p, floor)
+    assert lib.emg_stopping_epoch(None, 3, 5, 10, 0.0, ctypes.byref(ctypes.c_int32())) == emg.EMG_EINVAL
+    buf = (ctypes.c_double * 3)(1.0, 2.0, 3.0)
+    out = ctypes.c_int32()
+    assert lib.emg_stopping_epoch(buf, 3, 0, 10, 0.0, ctypes.byref(out)) == emg.EMG_EINVAL
+    assert lib.emg_stopping_epoch(buf, 3, 5, 10, -1.0, ctypes.byref(out)) == emg.EMG_EINVAL
+    assert lib.emg_stopping_epoch(buf, 0, 5, 10, 0.0, ctypes.byref(out)) == emg.EMG_OK and out.value == 0

@@ -336,3 +336,27 @@ def test_graph_replay_equals_direct_launches(lib, torch):
     assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
     c1.close()
     c2.close()
+
+
+def test_run_until_stops_where_the_rules_say(lib, torch):
+    """emg_run_until applies the stopping criterion (Sec. 4.1) and the noise-floor
+    rule (Sec. 4.3) to the misfit after each epoch."""
+    case = Case(n=96, m=32, side=5, noise_peak=1e3, seed=9)
+    p = oracle_params(alpha=0.05, minibatch=4)
+    ctx = make_context(lib, case, p)
+    hist = lib.emg_run_until(ctx.ctx, 60, window=3, patience=4)
+    assert 1 <= len(hist) <= 60
+    stop = O.stopping_epoch(list(hist), 3, 4)
+    assert (stop == len(hist)) if stop else (len(hist) == 60)
+    ctx.close()
+    # the noise floor: Phi at the true object and probe on the noisy data
+    ctx = make_context(lib, case, p)
+    truth = lib.Context(case.pos, case.d, case.n, case.n, lib.emg_default_params(alpha=0.05, minibatch=4),
+                        obj=torch.from_numpy(case.z_true), probe=torch.from_numpy(case.q_true))
+    floor = lib.emg_misfit(truth.ctx)
+    truth.close()
+    hist = lib.emg_run_until(ctx.ctx, 200, window=5, patience=10, floor=floor)
+    stop = O.stopping_epoch(list(hist), 5, 10, floor)
+    assert stop == len(hist) or len(hist) == 200
+    assert hist[-1] > 0
+    ctx.close()

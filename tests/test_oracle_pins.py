@@ -519,3 +519,34 @@ def test_whole_object_gradient_matches_central_differences():
     fq = _fd_wirtinger(lambda qq: O.misfit(qq, z, pos, a), Q, h=1e-6)
     assert np.max(np.abs(gz - fz)) < 1e-5 * np.max(np.abs(gz))
     assert np.max(np.abs(gq - fq)) < 1e-5 * np.max(np.abs(gq))
+
+
+# ---------------------------------------------------------------------------
+# Stopping criterion and noise-floor rule (Sec. 4.1, Sec. 4.3), hand-worked sequences
+
+def test_stopping_rule_never_fires_on_a_strictly_decreasing_residual():
+    r = [1.0 / t for t in range(1, 200)]
+    assert O.stopping_epoch(r, 5, 10) == 0
+
+
+def test_stopping_rule_on_a_constant_residual_fires_after_patience_checks():
+    # t = 5 sets the first average (no earlier best); t = 6 .. 15 are ten checks without improvement
+    assert O.stopping_epoch([1.0] * 40, 5, 10) == 15
+    assert O.stopping_epoch([1.0] * 40, 3, 4) == 7
+
+
+def test_stopping_rule_counts_from_the_last_improvement():
+    # averages: t=5: 3, t=6: 2.2, t=7: 1.6, t=8: 1.2, t=9: 1.0, then 1.0 from t = 10 on
+    r = [5, 4, 3, 2, 1] + [1] * 30
+    assert O.stopping_epoch(r, 5, 10) == 19
+    # an improvement in between restarts the count
+    r2 = [5, 4, 3, 2, 1] + [1] * 6 + [0.5] + [0.5] * 30
+    # t=12 average 0.9 < 1.0 resets; averages fall to 0.5 at t=16, then ten flat checks end at t=26
+    assert O.stopping_epoch(r2, 5, 10) == 26
+
+
+def test_noise_floor_rule_stops_at_the_first_residual_below_nine_tenths_of_the_floor():
+    r = [10.0, 5.0, 3.0, 2.5, 2.0]
+    assert O.stopping_epoch(r, 5, 10, floor=3.0) == 4     # 2.5 < 2.7
+    assert O.stopping_epoch(r, 5, 10, floor=2.0) == 0     # never below 1.8
+    assert O.stopping_epoch(r, 5, 10, floor=20.0) == 1    # 10 < 18 already
