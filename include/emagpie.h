@@ -100,7 +100,10 @@ typedef struct emg_problem {
  *             EMG_DFT_BF16X3: the pair as tensor-core GEMMs in BF16 with every
  *             operand split into high and low parts (see emg_dft2_bf16x3);
  *             m = 128 or 256 only (EMG_ENOTSUP otherwise).  The misfit of
- *             emg_misfit is always evaluated on the FP32 path.
+ *             emg_misfit is always evaluated on the FP32 path.  The tensor-
+ *             core kernels bound every wait; one that gives up is reported as
+ *             EMG_ETIMEOUT by the next call that synchronises (emg_misfit,
+ *             emg_run_epochs with host output, a sampled emg_step_minibatch).
  *  seed       schedule seed used when emg_run_epochs gets no order array.
  */
 typedef struct emg_params {
