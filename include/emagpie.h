@@ -91,7 +91,12 @@ typedef struct emg_problem {
  *               sum_k w_k z~_k / sum_k w_k, w_k(p) = |Q(p - o_k)|^2 + w_eps max|Q|^2,
  *             and the probe the mean of Q~_k over positions with max|z_k| > 0;
  *             EMG_COMBINE_SUM: z += sum_k (z~_k - z_k), Q += sum_k (Q~_k - Q).
- *  scatter    EMG_SCATTER_DETERMINISTIC (bitwise repeatable; only mode built).
+ *  scatter    EMG_SCATTER_DETERMINISTIC (default): the combine sums the B patches
+ *             of every object pixel in minibatch order (bitwise repeatable);
+ *             EMG_SCATTER_ATOMIC: the step kernel adds each patch into
+ *             object-sized FP32 accumulators with atomics and the combine only
+ *             finalises them (equal up to rounding order, not bitwise
+ *             repeatable; the weighted mean then needs w_eps > 0).
  *  joint      1: geometric-mean joint step (eMAGPIE); 0: take z+ and Q+ as they
  *             are (the rPIE-style simultaneous update of Sec. 2.2).
  *  w_eps      weight floor of the object combine, relative to max|Q|^2, >= 0.

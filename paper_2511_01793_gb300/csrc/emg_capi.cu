@@ -80,6 +80,9 @@ struct emg_ctx {
   float* d_amp_t = nullptr;       // [N][m][m] a_k transposed
   float2* d_tc_r = nullptr;       // [B][m][m] R_k
   double* d_tc_part = nullptr;    // [B][tiles] misfit partial sums
+  // atomic object scatter (par.scatter == EMG_SCATTER_ATOMIC)
+  float2* d_snum = nullptr;       // [n_rows][n_cols]
+  float* d_sden = nullptr;        // [n_rows][n_cols]
 
   std::vector<int32_t> h_pos;
   PrepArgs prep{};
@@ -183,8 +186,10 @@ emg_status validate_params(emg_ctx* c, const emg_params* p, int m, int n_pos) {
     return fail(c, EMG_EINVAL, "prolong must be EMG_PROLONG_CONST or EMG_PROLONG_BILINEAR");
   if (p->combine != EMG_COMBINE_WAVG && p->combine != EMG_COMBINE_SUM)
     return fail(c, EMG_EINVAL, "combine must be EMG_COMBINE_WAVG or EMG_COMBINE_SUM");
-  if (p->scatter == EMG_SCATTER_ATOMIC) return fail(c, EMG_ENOTSUP, "EMG_SCATTER_ATOMIC is not built");
-  if (p->scatter != EMG_SCATTER_DETERMINISTIC) return fail(c, EMG_EINVAL, "unknown scatter mode");
+  if (p->scatter != EMG_SCATTER_DETERMINISTIC && p->scatter != EMG_SCATTER_ATOMIC)
+    return fail(c, EMG_EINVAL, "unknown scatter mode");
+  if (p->scatter == EMG_SCATTER_ATOMIC && p->combine == EMG_COMBINE_WAVG && !(p->w_eps > 0.f))
+    return fail(c, EMG_EINVAL, "the atomic weighted-mean scatter needs w_eps > 0 (coverage is read from the weights)");
   if (p->joint != 0 && p->joint != 1) return fail(c, EMG_EINVAL, "joint must be 0 or 1");
   if (!(p->w_eps >= 0.f) || !isfinite(p->w_eps)) return fail(c, EMG_EINVAL, "w_eps must be finite and >= 0");
   if (p->dft != EMG_DFT_FFT32 && p->dft != EMG_DFT_BF16X3) return fail(c, EMG_EINVAL, "unknown dft mode");
@@ -230,6 +235,8 @@ void free_all(emg_ctx* c) {
   cudaFree(c->d_amp_t);
   cudaFree(c->d_tc_r);
   cudaFree(c->d_tc_part);
+  cudaFree(c->d_snum);
+  cudaFree(c->d_sden);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
 }
@@ -372,6 +379,10 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   sa.mu = c->d_mu;
   sa.phi = d_phi_out;
   sa.phi_after = c->d_phi_after;
+  sa.combine = c->par.combine;
+  sa.w_eps = c->par.w_eps;
+  sa.s_num = c->d_snum;
+  sa.s_den = c->d_sden;
   if (c->tc) {
     emg::TcStepArgs ta{};
     ta.object = c->object;
@@ -418,6 +429,8 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   aa.mq_next = c->d_mq + ((seq + 1) & 1);
   aa.tiles_x = (c->n_cols + emg::kApplyTile - 1) / emg::kApplyTile;
   aa.tiles_y = (c->n_rows + emg::kApplyTile - 1) / emg::kApplyTile;
+  aa.s_num = c->d_snum;
+  aa.s_den = c->d_sden;
   {
     LaunchMark mk(c, kKindApply);
     e = emg::launch_apply(aa, strm);
@@ -684,6 +697,13 @@ emg_status emg_create(emg_ctx** out, const emg_problem* pr, const emg_params* pa
   if (cudaMallocHost(&c->h_scalar, 64 * sizeof(double)) != cudaSuccess) return bail(EMG_ENOMEM);
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(EMG_ECUDA);
   if (alloc_levels(c) != EMG_OK) return bail(EMG_ENOMEM);
+  if (par->scatter == EMG_SCATTER_ATOMIC) {
+    const size_t npx = (size_t)c->n_rows * c->n_cols;
+    if (dmalloc(&c->d_snum, npx) || dmalloc(&c->d_sden, npx)) return bail(EMG_ENOMEM);
+    if (cudaMemsetAsync(c->d_snum, 0, npx * sizeof(float2), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->d_sden, 0, npx * sizeof(float), c->stream) != cudaSuccess)
+      return bail(EMG_ECUDA);
+  }
   if (par->dft == EMG_DFT_BF16X3) {
     if (emg::tc_work_create(&c->tc, m, B) != cudaSuccess || dmalloc(&c->d_amp_t, (size_t)N * mm) ||
         dmalloc(&c->d_tc_r, (size_t)B * mm) || dmalloc(&c->d_tc_part, (size_t)B * emg::tc_tiles_per_position(m)))

@@ -57,6 +57,12 @@ struct StepArgs {
   float* mu;                    // [b] max |z_k|^2
   double* phi;                  // [b] Phi_k at the snapshot
   double* phi_after;            // [b] Phi~_k(Q~, z~_k) (verify only)
+  // atomic object scatter (EMG_SCATTER_ATOMIC): z~_k goes straight into object-sized
+  // accumulators instead of zt; null for the deterministic scatter
+  int combine;
+  float w_eps;                  // weight floor of the weighted mean, relative to max|Q|^2
+  float2* s_num;                // [n_rows][n_cols] sum w z~ (weighted mean) or sum (z~ - z_k)
+  float* s_den;                 // [n_rows][n_cols] sum w (weighted mean)
   // tensor-core DFT path: R_k from outside and the misfit partial sums of each position
   const float2* r_in;           // [b][m][m] natural order, or null (FFT path)
   const double* r_partial;      // [b][r_tiles] sums of (|Psi| - a)^2
@@ -75,6 +81,8 @@ struct ApplyArgs {
   const float* wq;
   unsigned* mq_next;            // receives max|Q|^2 of the combined probe (atomicMax, float bits)
   int tiles_x, tiles_y;         // object tiles of kApplyTile x kApplyTile pixels
+  float2* s_num;                // atomic scatter: the step's accumulators, finalised and reset here
+  float* s_den;
 };
 
 // Forward-only cluster kernels (m up to 256): misfit partials, simulated

@@ -84,6 +84,20 @@ __device__ __forceinline__ float2 geometric_mean_aligned_fast(float2 x, float2 x
   return y;
 }
 
+// Atomic object scatter of one patch pixel (EMG_SCATTER_ATOMIC): weighted mean
+// (combine 0) adds w z~ and w, the summed corrections (combine 1) add z~ - z_k.
+__device__ __forceinline__ void scatter_atomic(float2* num, float* den, int combine, int n_rows, int n_cols, int gr,
+                                               int gc, float2 zn, float2 zk, float w) {
+  if ((unsigned)gr >= (unsigned)n_rows || (unsigned)gc >= (unsigned)n_cols) return;
+  const size_t gi = (size_t)gr * n_cols + gc;
+  if (combine == 0) {
+    atomicAdd(num + gi, make_float2(w * zn.x, w * zn.y));
+    atomicAdd(den + gi, w);
+  } else {
+    atomicAdd(num + gi, make_float2(zn.x - zk.x, zn.y - zk.y));
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T lerp4(T a, T b, T c, T d);
 template <>
@@ -559,6 +573,7 @@ __global__ void __launch_bounds__(StepThreads<M>::value) k_step(const StepArgs a
   // a5 (finest level) + a6 + a7: z+, Q+, geometric-mean joint step
   const float inv_mu = mu > 0.f ? 1.f / mu : 0.f;
   const float2* G0 = a.lv.G[0];
+  const float MQ = a.s_num ? __uint_as_float(*a.mq) : 0.f;  // combine weight of the atomic scatter
   float2* zt = a.zt + (size_t)kb * M * M;
   float2* qt = a.qt + (size_t)kb * M * M;
   float acc_after = 0.f;
@@ -586,7 +601,11 @@ __global__ void __launch_bounds__(StepThreads<M>::value) k_step(const StepArgs a
       zn = zplus;
       qn = qplus;
     }
-    zt[p] = zn;
+    if (a.s_num)
+      scatter_atomic(a.s_num, a.s_den, a.combine, a.n_rows, a.n_cols, o_r + r, o_c + c, zn, zk,
+                     fmaf(a.w_eps, MQ, cabs2(q)));
+    else
+      zt[p] = zn;
     qt[p] = qn;
     if (a.verify) acc_after += cabs2(csub(cmul(qn, zn), R));
   }
@@ -957,7 +976,10 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
       zn = zplus;
       qn = qplus;
     }
-    zt[r * M + c] = zn;
+    if (a.s_num)
+      scatter_atomic(a.s_num, a.s_den, a.combine, a.n_rows, a.n_cols, o_r + r, o_c + c, zn, zk, fmaf(a.w_eps, MQ, a2));
+    else
+      zt[r * M + c] = zn;
     qt[r * M + c] = qn;
     if (a.verify) acc_after += cabs2(csub(cmul(qn, zn), R));
   }
@@ -1280,7 +1302,28 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
   const int m = a.m;
   const size_t mm = (size_t)m * m;
   pdl_trigger();
-  if ((int)blockIdx.x < n_tiles) {
+  if ((int)blockIdx.x < n_tiles && a.s_num) {
+    // atomic scatter: the step kernel has accumulated this tile's sums; finalise and reset them
+    const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x % a.tiles_x;
+    const int row = ty * kApplyTile + tid / kApplyTile, col = tx * kApplyTile + tid % kApplyTile;
+    if (row >= a.n_rows || col >= a.n_cols) return;
+    pdl_wait();
+    const size_t gi = (size_t)row * a.n_cols + col;
+    if (a.combine == 0) {
+      const float den = a.s_den[gi];
+      if (den > 0.f) {
+        a.object[gi] = cscale(a.s_num[gi], 1.f / den);
+        a.s_num[gi] = czero();
+        a.s_den[gi] = 0.f;
+      }
+    } else {
+      const float2 dz = a.s_num[gi];
+      if (dz.x != 0.f || dz.y != 0.f) {
+        a.object[gi] = cadd(a.object[gi], dz);
+        a.s_num[gi] = czero();
+      }
+    }
+  } else if ((int)blockIdx.x < n_tiles) {
     const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x % a.tiles_x;
     const int r0 = ty * kApplyTile, c0 = tx * kApplyTile;
     if (tid == 0) total = 0;

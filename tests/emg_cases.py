@@ -61,12 +61,12 @@ def oracle_params(alpha=0.05, levels=1, minibatch=8, prolong="const", combine="w
                     combine=combine, w_eps=w_eps, joint=joint)
 
 
-def gpu_params(emg, p: O.Params, seed=0, dft=0):
+def gpu_params(emg, p: O.Params, seed=0, dft=0, scatter=0):
     return emg.emg_default_params(
         alpha=float(np.float32(p.alpha)), levels=p.levels, minibatch=p.minibatch,
         prolong=emg.EMG_PROLONG_CONST if p.prolong == "const" else emg.EMG_PROLONG_BILINEAR,
         combine=emg.EMG_COMBINE_WAVG if p.combine == "wavg" else emg.EMG_COMBINE_SUM,
-        joint=int(p.joint), w_eps=float(np.float32(p.w_eps)), seed=seed, dft=dft)
+        joint=int(p.joint), w_eps=float(np.float32(p.w_eps)), seed=seed, dft=dft, scatter=scatter)
 
 
 def oracle_inputs(case: Case, p: O.Params):
@@ -77,10 +77,10 @@ def oracle_inputs(case: Case, p: O.Params):
     return (case.z0.astype(np.complex128), case.q0.astype(np.complex128), case.pos, case.a64, q)
 
 
-def make_context(emg, case: Case, p: O.Params, seed=0, dft=0):
+def make_context(emg, case: Case, p: O.Params, seed=0, dft=0, scatter=0):
     import torch
 
-    ctx = emg.Context(case.pos, case.d, case.n, case.n, gpu_params(emg, p, seed, dft),
+    ctx = emg.Context(case.pos, case.d, case.n, case.n, gpu_params(emg, p, seed, dft, scatter),
                       obj=torch.from_numpy(case.z0), probe=torch.from_numpy(case.q0))
     return ctx
 

@@ -61,7 +61,7 @@ def _problem(m=32, n_pos=4):
     ("minibatch", 5, emg.EMG_EINVAL),       # > n_pos
     ("prolong", 7, emg.EMG_EINVAL),
     ("combine", 3, emg.EMG_EINVAL),
-    ("scatter", emg.EMG_SCATTER_ATOMIC, emg.EMG_ENOTSUP),
+    ("scatter", 2, emg.EMG_EINVAL),
     ("joint", 2, emg.EMG_EINVAL),
     ("w_eps", -1.0, emg.EMG_EINVAL),
     ("dft", 2, emg.EMG_EINVAL),
@@ -74,6 +74,12 @@ def test_create_rejects_bad_parameters_before_any_launch(lib, field, value, expe
     st = lib.emg_create(ctypes.byref(ctx), ctypes.byref(_problem()), ctypes.byref(p), None)
     assert st == expect
     assert ctx.value is None
+
+
+def test_atomic_weighted_mean_scatter_needs_a_weight_floor(lib):
+    p = emg.emg_default_params(scatter=emg.EMG_SCATTER_ATOMIC, w_eps=0.0)
+    ctx = ctypes.c_void_p()
+    assert lib.emg_create(ctypes.byref(ctx), ctypes.byref(_problem()), ctypes.byref(p), None) == emg.EMG_EINVAL
 
 
 def test_create_rejects_bad_problems(lib):

@@ -360,3 +360,46 @@ def test_run_until_stops_where_the_rules_say(lib, torch):
     assert stop == len(hist) or len(hist) == 200
     assert hist[-1] > 0
     ctx.close()
+
+
+ATOMIC_CASES = [
+    # m, levels, prolong, combine, dft, n_batch
+    (32, 2, "const", "wavg", 0, 12),
+    (32, 1, "const", "sum", 0, 5),
+    (128, 3, "bilinear", "wavg", 0, 6),
+    (256, 3, "bilinear", "wavg", 0, 4),
+    (128, 3, "bilinear", "wavg", 1, 6),
+]
+
+
+@pytest.mark.parametrize("m,levels,prolong,combine,dft,nb", ATOMIC_CASES)
+def test_atomic_scatter_matches_the_oracle_twice_in_a_row(lib, torch, m, levels, prolong, combine, dft, nb):
+    """EMG_SCATTER_ATOMIC: patches added into object-sized accumulators with FP32
+    atomics (any order), finalised by the combine.  Two minibatches in a row also
+    check that the accumulators are left at zero."""
+    case = Case(n=2 * m + 40, m=m, side=4, noise_peak=1e5 if m >= 64 else None, seed=m + 3 * levels)
+    p = oracle_params(alpha=0.05, levels=levels, minibatch=nb, prolong=prolong, combine=combine)
+    rng = np.random.default_rng(m + nb)
+    perm = rng.permutation(case.n_pos)
+    idx1, idx2 = [int(k) for k in perm[:nb]], [int(k) for k in perm[nb:2 * nb]]
+    ctx = make_context(lib, case, p, dft=dft, scatter=lib.EMG_SCATTER_ATOMIC)
+    det = make_context(lib, case, p, dft=dft)
+    zo, qo, pos, a, po = oracle_inputs(case, p)
+    tol = 1e-5 if dft == 0 else 4 * 3 * 2.0 ** -16
+    for step, idx in enumerate((idx1, idx2)):
+        z_before = state(ctx)[0]
+        lib.emg_step_minibatch(ctx.ctx, idx)
+        lib.emg_step_minibatch(det.ctx, idx)
+        z_g, q_g = state(ctx)
+        z_d, q_d = state(det)
+        zo, qo = O.minibatch_step(zo, qo, pos, a, idx, po)
+        mask = covered_mask(case, idx)
+        assert rel_err(z_g, zo, mask) <= tol and rel_err(q_g, qo) <= tol
+        assert rel_err(z_g, z_d, mask) <= 1e-6        # the two scatters differ by rounding order only
+        if step == 0:
+            assert np.array_equal(q_g, q_d)           # same probe combine from the same snapshot
+        else:
+            assert rel_err(q_g, q_d) <= 1e-6
+        assert np.array_equal(z_g[~mask], z_before[~mask])
+    ctx.close()
+    det.close()
