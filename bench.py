@@ -339,6 +339,29 @@ def run_gpu(args, world, rank, local):
         value = world * N * args.steps / (total_ms / 1e3)
         phi_end = emg.emg_misfit(ctx.ctx)
 
+        # the same epochs with the atomic object scatter (a variant; the default is deterministic)
+        pa = emg.emg_default_params(alpha=p["alpha"], levels=p["levels"], minibatch=B,
+                                    prolong=emg.EMG_PROLONG_BILINEAR if p["prolong"] == "bilinear"
+                                    else emg.EMG_PROLONG_CONST, seed=p["order_seed"] + rank,
+                                    scatter=emg.EMG_SCATTER_ATOMIC)
+        actx = emg.Context(w.pos, d, p["n"], p["n"], pa, obj=torch.from_numpy(z0), probe=torch.from_numpy(q0),
+                           stream=stream)
+        emg.emg_normalize_probe(actx.ctx)
+        emg.emg_set_cluster(actx.ctx, CLUSTER)
+        for _ in range(args.warmup):
+            emg.emg_run_epochs(actx.ctx, 1)
+        aev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        barrier()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            aev[i][0].record(stream)
+            emg.emg_run_epochs(actx.ctx, 1)
+            aev[i][1].record(stream)
+        barrier()
+        atomic_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in aev), world)
+        actx.close()
+
         # end-to-end through the host-buffer entry point (pinned host memory)
         e2e = None
         if not args.no_e2e:
@@ -388,6 +411,9 @@ def run_gpu(args, world, rank, local):
         "config": dict(workload_config(), parallelism=f"replicas{world}" if world > 1 else "single"),
         "e2e": e2e, "gpu_launches": launches_total, "roofline": roofline, "clocks": clk,
         "misfit_end": phi_end,
+        "scatter_atomic": {"value": world * N * args.steps / (atomic_ms / 1e3), "ms_per_step": atomic_ms / args.steps,
+                           "note": "EMG_SCATTER_ATOMIC (FP32 atomics, not bitwise repeatable); value above is the "
+                                   "deterministic default"},
     }
     if world == 1 and not args.no_cpu_baseline:
         rate, done, dt = cpu_oracle_sample(w, d, args.cpu_seconds)
