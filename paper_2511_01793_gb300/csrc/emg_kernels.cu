@@ -1730,8 +1730,11 @@ cudaError_t launch_amp_prep(const float* d, float* amp, int m, int n_pos, cudaSt
   return cudaGetLastError();
 }
 
+#ifndef EMG_PREP_TILE
+#define EMG_PREP_TILE 8
+#endif
 bool prep_tiled_config(PrepArgs& a) {
-  int tile = 16;
+  int tile = EMG_PREP_TILE;
   while (tile < (1 << (a.levels - 1))) tile *= 2;
   if (tile > a.m) tile = a.m;
   a.tile = tile;
