@@ -180,6 +180,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive floats (64-byte aligned) through the read-only path.
+__device__ __forceinline__ void load16(const float* p, float (&v)[16]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float4 t4 = __ldg(q + j);
+    v[4 * j] = t4.x;
+    v[4 * j + 1] = t4.y;
+    v[4 * j + 2] = t4.z;
+    v[4 * j + 3] = t4.w;
+  }
+}
+
 __device__ __forceinline__ uint32_t bf16_bits(float x) {
   return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
@@ -341,6 +354,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int local = 0;
     for (int pr = cl_id; pr < pairs; pr += n_cl, ++local) {
       const int buf = local & 1;
+      const int m_tile = 2 * (pr / a.tiles_n) + rank, n_tile = pr % a.tiles_n;
+      const int t = m_tile * a.tiles_n + n_tile;
+      const bool real = m_tile < a.m_tiles;  // the second half of the last block may lie past the rows
+      const int gr = m_tile * kBM + q * 32 + lane;  // global row
+      const int kb = gr / m, r = gr % m;
+      // modulus replacement: the first chunk's amplitudes are fetched while the MMAs still run
+      float am_next[16];
+      const float* amp_row = nullptr;
+      if constexpr (EPI == kEpiModulus) {
+        if (real) {
+          amp_row = a.amp_t + ((size_t)a.order[kb] * m + r) * m;
+          load16(amp_row + ((n_tile * kBN + c_lo) >> 1), am_next);
+        }
+      }
       const bool got = mbar_wait(&accf_bar[buf], (local >> 1) & 1, &abort_sh);
       if (!__all_sync(0xffffffffu, got)) {
         if (lane == 0) {
@@ -350,11 +377,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         break;
       }
       tc_fence_after();
-      const int m_tile = 2 * (pr / a.tiles_n) + rank, n_tile = pr % a.tiles_n;
-      const int t = m_tile * a.tiles_n + n_tile;
-      const bool real = m_tile < a.m_tiles;  // the second half of the last block may lie past the rows
-      const int gr = m_tile * kBM + q * 32 + lane;  // global row
-      const int kb = gr / m, r = gr % m;
       const uint32_t tb = tmem + (uint32_t)(buf * kBN) + ((uint32_t)(q * 32) << 16);
       float acc = 0.f;
 #pragma unroll 1
@@ -374,16 +396,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             a.out_lo[o] = lo;
           }
         } else if constexpr (EPI == kEpiModulus) {
-          const float4* ap = reinterpret_cast<const float4*>(a.amp_t + ((size_t)a.order[kb] * m + r) * m + u0);
           float am[16];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float4 t4 = __ldg(ap + j);
-            am[4 * j] = t4.x;
-            am[4 * j + 1] = t4.y;
-            am[4 * j + 2] = t4.z;
-            am[4 * j + 3] = t4.w;
-          }
+          for (int j = 0; j < 16; ++j) am[j] = am_next[j];
+          if (c0 + 32 < c_lo + kBN / 2) load16(amp_row + u0 + 16, am_next);  // the next chunk's, in flight
           uint32_t hi[16], lo[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {

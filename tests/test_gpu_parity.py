@@ -403,3 +403,55 @@ def test_atomic_scatter_matches_the_oracle_twice_in_a_row(lib, torch, m, levels,
         assert np.array_equal(z_g[~mask], z_before[~mask])
     ctx.close()
     det.close()
+
+
+@pytest.mark.parametrize("m,levels,prolong,nb", [(32, 2, "bilinear", 7), (128, 3, "bilinear", 5)])
+def test_rectangular_object_minibatch_matches_the_oracle(lib, torch, m, levels, prolong, nb):
+    """An object of n_rows != n_cols, with patches leaving it on every side (zero-padding of P_k)."""
+    import synth
+    from emg_cases import c64
+
+    rng = np.random.Generator(np.random.PCG64(m + 17))
+    n_rows, n_cols = 2 * m + 24, m + m // 2 + 8
+    z_true = c64(synth.make_object(n_rows, n_cols, rng, phi_max=1.2, sigma=3.0))
+    q_true = c64(synth.make_probe(m, radius=m / 3.2))
+    rows = np.arange(-m // 4, n_rows - m // 2, max(m // 3, 2))
+    cols = np.arange(-m // 3, n_cols - m // 3, max(m // 3, 2))
+    pos = np.array([(r, c) for r in rows for c in cols], dtype=np.int32)
+    d = np.ascontiguousarray(O.forward_intensity(q_true.astype(np.complex128), z_true.astype(np.complex128), pos),
+                             dtype=np.float32)
+    z0 = c64(synth.perturb(z_true, 0.3, rng))
+    q0 = c64(synth.perturb(q_true, 0.3, rng))
+    p = oracle_params(alpha=0.05, levels=levels, minibatch=nb, prolong=prolong)
+    idx = [int(k) for k in rng.permutation(len(pos))[:nb]]
+    ctx = lib.Context(pos, d, n_rows, n_cols, gpu_params(lib, p), obj=torch.from_numpy(z0), probe=torch.from_numpy(q0))
+    lib.emg_step_minibatch(ctx.ctx, idx)
+    z_g, q_g = state(ctx)
+    ctx.close()
+    po = O.Params(alpha=float(np.float32(p.alpha)), levels=levels, minibatch=nb, prolong=prolong,
+                  w_eps=float(np.float32(p.w_eps)))
+    z_o, q_o = O.minibatch_step(z0.astype(np.complex128), q0.astype(np.complex128), pos,
+                                np.sqrt(np.maximum(d.astype(np.float64), 0.0)), idx, po)
+    mask = np.zeros((n_rows, n_cols), dtype=bool)
+    for k in idx:
+        r0, c0 = pos[k]
+        mask[max(r0, 0):max(min(r0 + m, n_rows), 0), max(c0, 0):max(min(c0 + m, n_cols), 0)] = True
+    assert rel_err(z_g, z_o, mask) <= STEP_TOL and rel_err(q_g, q_o) <= STEP_TOL
+    assert np.array_equal(z_g[~mask], z0.astype(np.complex128)[~mask])
+
+
+@pytest.mark.parametrize("m,levels,nb", [(256, 6, 2), (256, 3, 1)])
+def test_deepest_hierarchy_and_single_position_at_the_largest_probe(lib, torch, m, levels, nb):
+    """m = 256 at its deepest supported multigrid (L = 6: 8 px at the coarsest level,
+    one row per CTA of the 8-CTA cluster) and a minibatch of one position."""
+    case = Case(n=2 * m + 40, m=m, side=3, noise_peak=1e5, seed=levels + nb)
+    p = oracle_params(alpha=0.05, levels=levels, minibatch=nb, prolong="bilinear")
+    idx = [0, case.n_pos - 3][:nb]
+    ctx = make_context(lib, case, p)
+    lib.emg_step_minibatch(ctx.ctx, idx)
+    z_g, q_g = state(ctx)
+    ctx.close()
+    zo, qo, pos, a, po = oracle_inputs(case, p)
+    z_o, q_o = O.minibatch_step(zo, qo, pos, a, idx, po)
+    mask = covered_mask(case, idx)
+    assert rel_err(z_g, z_o, mask) <= STEP_TOL and rel_err(q_g, q_o) <= STEP_TOL
