@@ -45,7 +45,7 @@ typedef enum emg_status {
   EMG_ENOMEM = 2,   /* device or pinned host allocation failed */
   EMG_ECUDA = 3,    /* a CUDA call or kernel failed */
   EMG_ETIMEOUT = 4, /* a bounded device wait gave up */
-  EMG_ENOTSUP = 5   /* valid request that this build does not implement */
+  EMG_ENOTSUP = 5   /* valid request that this library does not implement */
 } emg_status;
 
 enum { EMG_PROLONG_CONST = 0, EMG_PROLONG_BILINEAR = 1 };

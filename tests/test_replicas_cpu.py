@@ -1,5 +1,5 @@
 """The N > 1 path of bench.py without a GPU: world-size-2 process groups on
-gloo.  The method's minibatches do not shard across GPUs in this build
+gloo.  The method's minibatches do not shard across GPUs in this library
 (replicas only), so the only cross-rank step is the timing reduction (the
 slowest rank's time) and rank 0 printing the single result line."""
 import json
