@@ -103,3 +103,51 @@ def test_batch_of_uneven_problems_equals_individual_runs(lib, torch):
     lib.emg_batch_destroy(b)
     for c in batch_ctx + solo_ctx:
         c.close()
+
+
+def test_batch_with_tensor_core_dft_contexts_equals_individual_runs(lib, torch):
+    """Contexts on the tensor-core DFT path (two-CTA cluster kernels, TMA,
+    bounded waits) inside one batch graph, beside an FP32 one."""
+    specs = [  # m, n, side, levels, prolong, minibatch, dft
+        (128, 300, 3, 2, "bilinear", 4, 1),
+        (256, 560, 2, 3, "bilinear", 3, 1),
+        (128, 280, 3, 3, "bilinear", 5, 0),
+    ]
+    cases, params, dfts = [], [], []
+    for i, (m, n, side, levels, prolong, B, dft) in enumerate(specs):
+        cases.append(Case(n=n, m=m, side=side, noise_peak=1e4, seed=90 + i))
+        params.append(oracle_params(minibatch=B, levels=levels, prolong=prolong))
+        dfts.append(dft)
+    batch_ctx = [make_context(lib, c, p, seed=200 + i, dft=d) for i, (c, p, d) in enumerate(zip(cases, params, dfts))]
+    solo_ctx = [make_context(lib, c, p, seed=200 + i, dft=d) for i, (c, p, d) in enumerate(zip(cases, params, dfts))]
+    b = lib.emg_batch_create([c.ctx for c in batch_ctx])
+    lib.emg_batch_run_epochs(b, 2)
+    for c in solo_ctx:
+        lib.emg_run_epochs(c.ctx, 2)
+    for cb, cs in zip(batch_ctx, solo_ctx):
+        zb, qb = state(cb)
+        zs, qs = state(cs)
+        assert np.array_equal(zb, zs) and np.array_equal(qb, qs)
+    lib.emg_batch_destroy(b)
+    for c in batch_ctx + solo_ctx:
+        c.close()
+
+
+def test_autotune_on_the_tensor_core_path_keeps_results(lib, torch):
+    """The tiling autotuner on a tensor-core DFT context (m = 128: 2 or 4 CTAs per
+    position in the step kernel that follows the transforms)."""
+    case = Case(n=300, m=128, side=3, noise_peak=1e4, seed=97)
+    p = oracle_params(minibatch=4, levels=3, prolong="bilinear")
+    tuned = make_context(lib, case, p, dft=1)
+    plain = make_context(lib, case, p, dft=1)
+    chosen, ms = lib.emg_autotune(tuned.ctx)
+    assert chosen in (2, 4) and ms > 0
+    z0, q0 = state(tuned)
+    assert np.array_equal(z0, case.z0.astype(np.complex128))      # the bound state is left alone
+    lib.emg_run_epochs(tuned.ctx, 2)
+    lib.emg_run_epochs(plain.ctx, 2)
+    zt, qt = state(tuned)
+    zp, qp = state(plain)
+    assert np.array_equal(zt, zp) and np.array_equal(qt, qp)      # tilings agree bitwise for m >= 64
+    tuned.close()
+    plain.close()
