@@ -93,6 +93,16 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+# FP32 pipe peak derived from the unit counts: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def step_flops_per_position(m: int, levels: int) -> float:
+    """Algorithmic FLOPs of one position: two 2-D FFTs (5 N log2 N each, N = m^2) plus about
+    100 per pixel of pointwise and multigrid work on every level (1 + 1/4 + 1/16 ...)."""
+    return 10.0 * m * m * math.log2(m * m) + 100.0 * m * m * sum(4.0 ** -l for l in range(levels))
+
+
 def recorded_traffic():
     """DRAM bytes per step-kernel launch from the committed ncu summary, if still current.
 
@@ -401,6 +411,10 @@ def run_gpu(args, world, rank, local):
                 "avg_launch_us": round(avg_launch_s * 1e6, 3), "launch_share": kernel_share,
                 "timing": "CUDA events around each k_step launch over a second pass of the same "
                           f"{args.steps} epochs (direct launches, {prof_ms / args.steps:.3f} ms/epoch)"}
+    flops = step_flops_per_position(m, p["levels"]) * pos_per_launch
+    roofline["fp32"] = {"achieved": round(flops / avg_launch_s / 1e12, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
+                        "unit": "TFLOP/s", "frac": round(flops / avg_launch_s / 1e12 / FP32_PEAK_TFLOPS, 5),
+                        "flops_per_launch": int(flops), "peak_source": "derived: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
 
     if rank != 0:
         return

@@ -299,9 +299,10 @@ emg_status emg_dft2_bf16x3(const float* in, float* out, int32_t m, int32_t count
 
 /*
  * FFT tiling: the number of CTAs that share one scan position in the step
- * kernel (1 for m <= 32; 2 or 4 for m = 64, 128; 8 for m = 256).  It changes
- * speed only: results are identical for every valid choice.  EMG_ENOTSUP when
- * the choice is not built or leaves a CTA without a row at the coarsest level.
+ * kernel (1 or 2 for m <= 32; 2 or 4 for m = 64; 2, 4 or 8 for m = 128; 8 for
+ * m = 256).  It changes speed only: results are identical for every valid
+ * choice.  EMG_ENOTSUP when the choice is not built or leaves a CTA without a
+ * row at the coarsest level.
  */
 emg_status emg_set_cluster(emg_ctx* ctx, int32_t cluster);
 

@@ -1847,6 +1847,7 @@ cudaError_t set_cluster_attrs() {
   if ((e = set_cluster_smem(k_stepc<32, 2>, CTile<32, 2>::smem_elems)) != cudaSuccess) return e;
   if ((e = set_cluster_smem(k_stepc<64, 4>, CTile<64, 4>::smem_elems)) != cudaSuccess) return e;
   if ((e = set_cluster_smem(k_stepc<128, 4>, CTile<128, 4>::smem_elems)) != cudaSuccess) return e;
+  if ((e = set_cluster_smem(k_stepc<128, 8>, CTile<128, 8>::smem_elems)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_stepc<64, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(CTile<64, 2>::smem_elems * sizeof(float2)))) != cudaSuccess)
     return e;
@@ -1858,6 +1859,7 @@ cudaError_t set_cluster_attrs() {
     return e;
   if ((e = set_cluster_smem(k_stepc<128, 2, true>, CTile<128, 2>::smem_elems)) != cudaSuccess) return e;
   if ((e = set_cluster_smem(k_stepc<128, 4, true>, CTile<128, 4>::smem_elems)) != cudaSuccess) return e;
+  if ((e = set_cluster_smem(k_stepc<128, 8, true>, CTile<128, 8>::smem_elems)) != cudaSuccess) return e;
   if ((e = set_cluster_smem(k_stepc<256, 8, true>, CTile<256, 8>::smem_elems)) != cudaSuccess) return e;
   if ((e = set_cluster_smem(k_fwdc<256, 8, 0>, CTile<256, 8>::smem_elems)) != cudaSuccess) return e;
   if ((e = set_cluster_smem(k_fwdc<256, 8, 1>, CTile<256, 8>::smem_elems)) != cudaSuccess) return e;
@@ -1896,6 +1898,7 @@ cudaError_t launch_step_rin(int m, int b, const StepArgs& a, cudaStream_t s) {
   switch (m * 16 + a.cluster) {
     case 128 * 16 + 2: return launch_stepc_rin_t<128, 2>(b, a, s);
     case 128 * 16 + 4: return launch_stepc_rin_t<128, 4>(b, a, s);
+    case 128 * 16 + 8: return launch_stepc_rin_t<128, 8>(b, a, s);
     case 256 * 16 + 8: return launch_stepc_rin_t<256, 8>(b, a, s);
     default: return cudaErrorInvalidValue;
   }
@@ -1911,6 +1914,7 @@ cudaError_t launch_step(int m, int b, const StepArgs& a, cudaStream_t s) {
     case 64 * 16 + 4: return launch_stepc_t<64, 4>(b, a, s);
     case 128 * 16 + 2: return launch_stepc_t<128, 2>(b, a, s);
     case 128 * 16 + 4: return launch_stepc_t<128, 4>(b, a, s);
+    case 128 * 16 + 8: return launch_stepc_t<128, 8>(b, a, s);
     case 256 * 16 + 8: return launch_stepc_t<256, 8>(b, a, s);
     default: return cudaErrorInvalidValue;
   }
@@ -2027,7 +2031,7 @@ cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t s) {
 // supports `levels` multigrid levels.
 bool step_supported(int m, int levels, int cluster) {
   const bool built = (cluster == 1 && m <= 32) || (cluster == 2 && m <= 128) || (cluster == 4 && (m == 64 || m == 128)) ||
-                     (cluster == 8 && m == 256);
+                     (cluster == 8 && m >= 128);
   if (!built) return false;
   if (cluster == 1) return step_smem_bytes(m, levels) <= (size_t)step_smem_limit();
   if ((m >> (levels - 1)) < cluster) return false;  // every CTA needs a row at the coarsest level

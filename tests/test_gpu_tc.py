@@ -151,6 +151,22 @@ def test_tc_epochs_are_bitwise_repeatable(lib, torch):
     assert np.array_equal(res[0][2][1], res[1][2][1])
 
 
+def test_tc_step_is_the_same_for_every_fft_tiling(lib, torch):
+    """The cluster size of the step kernel that consumes R_k does not change the results."""
+    m = 128
+    case = Case(n=2 * m + 40, m=m, side=4, noise_peak=1e5, seed=7)
+    p = oracle_params(alpha=0.05, levels=3, minibatch=8, prolong="bilinear")
+    res = []
+    for cl in (2, 4, 8):
+        ctx = make_context(lib, case, p, dft=1)
+        lib.emg_set_cluster(ctx.ctx, cl)
+        lib.emg_run_epochs(ctx.ctx, 2)
+        res.append(state(ctx))
+        ctx.close()
+    for z, q in res[1:]:
+        assert np.array_equal(z, res[0][0]) and np.array_equal(q, res[0][1])
+
+
 def test_full_size_precision_minibatch_matches_the_oracle(lib, torch):
     """One minibatch of the precision workload at full size (object 2048^2,
     probe 256^2, B = 256, L = 3 bilinear) in the launch configuration the bench
