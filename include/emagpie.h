@@ -143,8 +143,11 @@ emg_status emg_create(emg_ctx** out, const emg_problem* problem,
 
 /*
  * Replaces the data d_k (same shape as at creation).  `intensity` may be a
- * device pointer or a host pointer (pinned host memory copies asynchronously;
- * pageable memory is staged synchronously).
+ * device pointer or a host pointer.  Pinned host memory is read in place by
+ * the amplitude kernel, asynchronously on the context's stream (through a
+ * device staging copy on the tensor-core DFT path); pageable memory is staged
+ * synchronously.  The caller keeps pinned data unchanged until the stream has
+ * passed this call.
  */
 emg_status emg_set_intensity(emg_ctx* ctx, const float* intensity);
 
@@ -253,11 +256,11 @@ emg_status emg_run_until(emg_ctx* ctx, int32_t max_epochs, int32_t window, int32
 emg_status emg_schedule_permutation(uint64_t seed, int64_t epoch, int32_t n, int32_t* out);
 
 /*
- * End-to-end call on host buffers: copies intensity (host [n_pos][m][m]),
- * object (host complex64 [n_rows][n_cols]) and probe (host complex64 [m][m])
- * to library-owned device buffers, runs n_epochs as emg_run_epochs does and
- * copies object and probe back.  The context's bound device state is not
- * touched.  Synchronises.
+ * End-to-end call on host buffers: takes intensity (host [n_pos][m][m]) as
+ * emg_set_intensity does, copies object (host complex64 [n_rows][n_cols]) and
+ * probe (host complex64 [m][m]) to library-owned device buffers, runs
+ * n_epochs as emg_run_epochs does and copies object and probe back.  The
+ * context's bound device state is not touched.  Synchronises.
  */
 emg_status emg_reconstruct_host(emg_ctx* ctx, const float* intensity, float* object,
                                 float* probe, int32_t n_epochs, const int32_t* order,

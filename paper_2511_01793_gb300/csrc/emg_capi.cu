@@ -20,6 +20,17 @@ using emg::StepArgs;
 // Kernel kinds counted and timed by the profiling hooks.
 enum { kKindPrep = 0, kKindStep = 1, kKindApply = 2, kKindOther = 3, kKindDft = 4, kKinds = 5 };
 
+// A captured epoch and the state it was captured for.
+struct EpochGraph {
+  cudaGraphExec_t exec = nullptr;
+  float2* object = nullptr;
+  float2* probe = nullptr;
+  int verify = -1;
+  int cluster = -1;
+  const float* src = nullptr;
+  int64_t counts[kKinds] = {0, 0, 0, 0, 0};
+};
+
 struct emg_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -49,14 +60,15 @@ struct emg_ctx {
   unsigned* d_mq = nullptr;       // [2] max|Q|^2 slots (float bits), alternating per minibatch
   int32_t* d_epoch_order = nullptr;  // [N] order read by the captured epoch graph
 
-  // One epoch captured as a CUDA graph (replayed per epoch on `stream`).
+  // One epoch captured as a CUDA graph (replayed per epoch on `stream`), and
+  // the variant that also reads each minibatch's data from pinned host memory.
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t graph = nullptr;
-  float2* graph_object = nullptr;
-  float2* graph_probe = nullptr;
-  int graph_verify = -1;
-  int graph_cluster = -1;
-  int64_t graph_counts[kKinds] = {0, 0, 0, 0, 0};
+  EpochGraph graph, sgraph;
+  // While the streamed variant is captured: its host source, the side stream
+  // that reads it ahead of the step kernels, and the event that orders them.
+  const float* stream_src = nullptr;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_side = nullptr;
   float* d_wq = nullptr;          // [m][m]
   void* d_levels = nullptr;       // all multigrid arrays
   int32_t* d_orders = nullptr;    // [cap_orders]
@@ -220,8 +232,11 @@ void free_all(emg_ctx* c) {
   cudaFree(c->d_norm);
   cudaFree(c->d_mq);
   cudaFree(c->d_epoch_order);
-  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+  if (c->sgraph.exec) cudaGraphExecDestroy(c->sgraph.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_side) cudaEventDestroy(c->ev_side);
   cudaFree(c->d_wq);
   cudaFree(c->d_levels);
   cudaFree(c->d_orders);
@@ -353,11 +368,20 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   pa.mq_read = c->d_mq + (seq & 1);
   pa.mq_next = c->d_mq + ((seq + 1) & 1);
   cudaError_t e;
+  if (c->stream_src) {  // this minibatch's amplitudes, read from host memory on the side stream
+    {
+      LaunchMark mk(c, kKindOther);
+      e = emg::launch_amp_gather(c->stream_src, d_idx, b, c->d_amp, c->m, c->side);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "k_amp_gather launch");
+    EMG_CUDA(c, cudaEventRecord(c->ev_side, c->side));
+  }
   {
     LaunchMark mk(c, kKindPrep);
     e = emg::launch_prep(pa, strm);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_prep launch");
+  if (c->stream_src) EMG_CUDA(c, cudaStreamWaitEvent(strm, c->ev_side, 0));
   StepArgs sa{};
   sa.object = c->object;
   sa.probe = c->probe;
@@ -458,6 +482,10 @@ emg_status check_bound(emg_ctx* c) {
 // and every minibatch (used inside graph capture).
 emg_status enqueue_epoch(emg_ctx* c, cudaStream_t s) {
   emg_status st = seed_probe_max(c, s);
+  if (st == EMG_OK && c->stream_src) {
+    EMG_CUDA(c, cudaEventRecord(c->ev_side, s));
+    EMG_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_side, 0));
+  }
   const int N = c->n_pos, B = c->par.minibatch;
   int seq = 0;
   for (int b0 = 0; st == EMG_OK && b0 < N; b0 += B) {
@@ -469,22 +497,26 @@ emg_status enqueue_epoch(emg_ctx* c, cudaStream_t s) {
 
 // Captures one epoch (probe-max seed + all minibatches reading d_epoch_order)
 // as a graph for the currently bound state; reused until the state changes.
-emg_status ensure_epoch_graph(emg_ctx* c) {
-  if (c->graph && c->graph_object == c->object && c->graph_probe == c->probe &&
-      c->graph_verify == c->verify && c->graph_cluster == c->cluster)
+// With `src` (pinned host intensities) each minibatch's amplitudes are read
+// from it on the side stream, and the minibatch's step waits for them.
+emg_status ensure_epoch_graph(emg_ctx* c, EpochGraph& G, const float* src) {
+  if (G.exec && G.object == c->object && G.probe == c->probe && G.verify == c->verify &&
+      G.cluster == c->cluster && G.src == src)
     return EMG_OK;
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
+  if (G.exec) {
+    cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
   }
   int64_t before[kKinds];
   for (int i = 0; i < kKinds; ++i) before[i] = c->launches[i];
   EMG_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  c->stream_src = src;
   emg_status st = enqueue_epoch(c, c->cap_stream);
+  c->stream_src = nullptr;
   cudaGraph_t g = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
   for (int i = 0; i < kKinds; ++i) {
-    c->graph_counts[i] = c->launches[i] - before[i];
+    G.counts[i] = c->launches[i] - before[i];
     c->launches[i] = before[i];
   }
   if (st != EMG_OK) {
@@ -492,21 +524,25 @@ emg_status ensure_epoch_graph(emg_ctx* c) {
     return st;
   }
   if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaStreamEndCapture");
-  const cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
+  const cudaError_t ie = cudaGraphInstantiate(&G.exec, g, 0);
   cudaGraphDestroy(g);
   if (ie != cudaSuccess) {
-    c->graph = nullptr;
+    G.exec = nullptr;
     return cuda_fail(c, ie, "cudaGraphInstantiate");
   }
-  c->graph_object = c->object;
-  c->graph_probe = c->probe;
-  c->graph_verify = c->verify;
-  c->graph_cluster = c->cluster;
+  G.object = c->object;
+  G.probe = c->probe;
+  G.verify = c->verify;
+  G.cluster = c->cluster;
+  G.src = src;
   return EMG_OK;
 }
 
+// `stream_src`: pinned host intensities that epoch 0 reads minibatch by
+// minibatch (graph path only; the amplitudes of all positions are in place
+// after it, since an epoch visits every position).
 emg_status run_epochs_impl(emg_ctx* c, int32_t n_epochs, const int32_t* order, double* running,
-                           double* misfit) {
+                           double* misfit, const float* stream_src = nullptr) {
   if (n_epochs < 0) return fail(c, EMG_EINVAL, "n_epochs < 0");
   if (n_epochs == 0) return EMG_OK;
   const int N = c->n_pos, B = c->par.minibatch;
@@ -532,14 +568,18 @@ emg_status run_epochs_impl(emg_ctx* c, int32_t n_epochs, const int32_t* order, d
   // Profiling times each launch with events, so it runs the epochs as direct
   // launches; otherwise each epoch replays the captured graph.
   const bool use_graph = !c->profile;
-  if (use_graph && (st = ensure_epoch_graph(c)) != EMG_OK) return st;
+  if (!use_graph && stream_src) return fail(c, EMG_EINVAL, "streamed intensities need the graph path");
+  if (use_graph && stream_src && (st = ensure_epoch_graph(c, c->sgraph, stream_src)) != EMG_OK) return st;
+  if (use_graph && (n_epochs > 1 || !stream_src) && (st = ensure_epoch_graph(c, c->graph, nullptr)) != EMG_OK)
+    return st;
   for (int32_t e = 0; e < n_epochs; ++e) {
     const int32_t* ord = c->d_orders + (size_t)e * N;
     if (use_graph) {
+      const EpochGraph& G = (e == 0 && stream_src) ? c->sgraph : c->graph;
       EMG_CUDA(c, cudaMemcpyAsync(c->d_epoch_order, ord, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToDevice,
                                   c->stream));
-      EMG_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
-      for (int i = 0; i < kKinds; ++i) c->launches[i] += c->graph_counts[i];
+      EMG_CUDA(c, cudaGraphLaunch(G.exec, c->stream));
+      for (int i = 0; i < kKinds; ++i) c->launches[i] += G.counts[i];
     } else {
       if ((st = seed_probe_max(c, c->stream)) != EMG_OK) return st;
       int seq = 0;
@@ -607,10 +647,25 @@ int32_t stopping_epoch(const double* r, int n, int window, int patience, double 
   return 0;
 }
 
+// Device address through which a kernel may read pinned, mapped host memory
+// (over the CPU-GPU link), or NULL for any other pointer.
+const float* mapped_host_pointer(const float* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? (const float*)at.devicePointer : nullptr;
+}
+
 emg_status set_intensity_impl(emg_ctx* c, const float* intensity) {
   const size_t n = (size_t)c->n_pos * c->m * c->m;
   const float* src = intensity;
-  if (!is_device_pointer(intensity)) {
+  const float* mapped = (c->tc || is_device_pointer(intensity)) ? nullptr : mapped_host_pointer(intensity);
+  if (mapped) {
+    // pinned host data: the amplitude kernel reads it in place, one pass over the link
+    src = mapped;
+  } else if (!is_device_pointer(intensity)) {
     if (!c->d_stage_d && cudaMalloc(&c->d_stage_d, n * sizeof(float)) != cudaSuccess)
       return fail(c, EMG_ENOMEM, "cudaMalloc(intensity staging) failed");
     EMG_CUDA(c, cudaMemcpyAsync(c->d_stage_d, intensity, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
@@ -695,7 +750,10 @@ emg_status emg_create(emg_ctx** out, const emg_problem* pr, const emg_params* pa
       dmalloc(&c->d_wq, mm))
     return bail(EMG_ENOMEM);
   if (cudaMallocHost(&c->h_scalar, 64 * sizeof(double)) != cudaSuccess) return bail(EMG_ENOMEM);
-  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(EMG_ECUDA);
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_side, cudaEventDisableTiming) != cudaSuccess)
+    return bail(EMG_ECUDA);
   if (alloc_levels(c) != EMG_OK) return bail(EMG_ENOMEM);
   if (par->scatter == EMG_SCATTER_ATOMIC) {
     const size_t npx = (size_t)c->n_rows * c->n_cols;
@@ -881,7 +939,12 @@ emg_status emg_reconstruct_host(emg_ctx* c, const float* intensity, float* objec
     return fail(c, EMG_ENOMEM, "cudaMalloc(object) failed");
   if (!c->d_own_probe && cudaMalloc(&c->d_own_probe, nq * sizeof(float2)) != cudaSuccess)
     return fail(c, EMG_ENOMEM, "cudaMalloc(probe) failed");
-  emg_status st = set_intensity_impl(c, intensity);
+  // Pinned host intensities on the FFT path are read minibatch by minibatch
+  // during the first epoch, overlapping the transfer with the earlier steps.
+  const float* streamed = (n_epochs > 0 && !c->tc && !c->profile && !is_device_pointer(intensity))
+                              ? mapped_host_pointer(intensity)
+                              : nullptr;
+  emg_status st = streamed ? EMG_OK : set_intensity_impl(c, intensity);
   if (st != EMG_OK) return st;
   EMG_CUDA(c, cudaMemcpyAsync(c->d_own_object, object, nz * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
   EMG_CUDA(c, cudaMemcpyAsync(c->d_own_probe, probe, nq * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
@@ -889,7 +952,7 @@ emg_status emg_reconstruct_host(emg_ctx* c, const float* intensity, float* objec
   float2* keep_p = c->probe;
   c->object = c->d_own_object;
   c->probe = c->d_own_probe;
-  st = run_epochs_impl(c, n_epochs, order, running_misfit, misfit);
+  st = run_epochs_impl(c, n_epochs, order, running_misfit, misfit, streamed);
   c->object = keep_o;
   c->probe = keep_p;
   if (st != EMG_OK) return st;
@@ -1150,7 +1213,7 @@ emg_status emg_batch_run_epochs(emg_batch* b, int32_t n_epochs, emg_stream_t str
       for (int k2 = 0; k2 < kKinds; ++k2) before[k2] = c->launches[k2];
       st = enqueue_epoch(c, b->forks[i]);
       for (int k2 = 0; k2 < kKinds; ++k2) {
-        c->graph_counts[k2] = c->launches[k2] - before[k2];
+        c->graph.counts[k2] = c->launches[k2] - before[k2];
         c->launches[k2] = before[k2];
       }
       c->profile = keep_profile;
@@ -1181,7 +1244,7 @@ emg_status emg_batch_run_epochs(emg_batch* b, int32_t n_epochs, emg_stream_t str
   for (int32_t e = 0; e < n_epochs; ++e) {
     if (cudaGraphLaunch(b->graph, s) != cudaSuccess) return EMG_ECUDA;
     for (emg_ctx* c : b->ctxs)
-      for (int k2 = 0; k2 < kKinds; ++k2) c->launches[k2] += c->graph_counts[k2];
+      for (int k2 = 0; k2 < kKinds; ++k2) c->launches[k2] += c->graph.counts[k2];
   }
   for (emg_ctx* c : b->ctxs) c->epoch += n_epochs;
   return cudaGetLastError() == cudaSuccess ? EMG_OK : EMG_ECUDA;

@@ -138,6 +138,8 @@ constexpr int kApplyProbeGroups = 8;    // probe blocks: 32 pixels x 8 position 
 
 cudaError_t upload_twiddles();
 cudaError_t launch_amp_prep(const float* d, float* amp, int m, int n_pos, cudaStream_t s);
+// a_k of positions idx[0..b) (device indices) from d, which may be mapped host memory.
+cudaError_t launch_amp_gather(const float* d, const int32_t* idx, int b, float* amp, int m, cudaStream_t s);
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 cudaError_t launch_probe_max(const float2* probe, int m, unsigned* slot, cudaStream_t s);
 // Fills tile/halo of a and returns true when the tiled prep fits in shared memory.

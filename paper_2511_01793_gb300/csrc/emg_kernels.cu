@@ -169,15 +169,84 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // ---------------------------------------------------------------------------
 // a_k in storage order: amp[k][e_r][e_c] = sqrt(max(d[k][f(e_r)][f(e_c)], 0)).
 template <int M>
-__global__ void k_amp_prep(const float* __restrict__ d, float* __restrict__ amp, int n_pos) {
-  const size_t total = (size_t)n_pos * M * M;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const size_t k = i / (M * M);
-    const int e = (int)(i % (M * M));
-    const int er = e / M, ec = e % M;
-    const float v = d[k * M * M + storage_to_freq<M>(er) * M + storage_to_freq<M>(ec)];
-    amp[i] = sqrtf(fmaxf(v, 0.f));
+__global__ void __launch_bounds__(256) k_amp_prep(const float* __restrict__ d, float* __restrict__ amp,
+                                                  int n_pos) {
+  // One warp per storage row: the frequency row it needs is read whole with
+  // consecutive lanes on consecutive words (the source may be host memory read
+  // over the CPU-GPU link), then permuted through shared memory.
+  constexpr int PL = (M + 31) / 32;
+  __shared__ float rows[8][M];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* buf = rows[warp];
+  const size_t n_rows = (size_t)n_pos * M;
+  for (size_t g = (size_t)blockIdx.x * 8 + warp; g < n_rows; g += (size_t)gridDim.x * 8) {
+    const size_t k = g / M;
+    const int er = (int)(g % M);
+    const float* src = d + (k * M + storage_to_freq<M>(er)) * M;
+    float v[PL];
+#pragma unroll
+    for (int j = 0; j < PL; ++j)
+      if (lane + 32 * j < M) v[j] = src[lane + 32 * j];
+#pragma unroll
+    for (int j = 0; j < PL; ++j)
+      if (lane + 32 * j < M) buf[lane + 32 * j] = v[j];
+    __syncwarp();
+    float* dst = amp + g * M;
+#pragma unroll
+    for (int j = 0; j < PL; ++j) {
+      const int ec = lane + 32 * j;
+      if (ec < M) dst[ec] = sqrtf(fmaxf(buf[storage_to_freq<M>(ec)], 0.f));
+    }
+    __syncwarp();
+  }
+}
+
+// a_k of the positions idx[0..b) into their slots of amp, read from d (any
+// device-readable address, e.g. pinned host memory).  A small grid that runs
+// beside the step kernels: each warp keeps kGatherRows rows of loads in flight.
+#ifndef EMG_GATHER_BLOCKS
+#define EMG_GATHER_BLOCKS 152
+#endif
+#ifndef EMG_GATHER_ROWS
+#define EMG_GATHER_ROWS 2
+#endif
+constexpr int kGatherRows = EMG_GATHER_ROWS, kGatherWarps = 4, kGatherBlocks = EMG_GATHER_BLOCKS;
+template <int M>
+__global__ void __launch_bounds__(kGatherWarps * 32) k_amp_gather(const float* __restrict__ d,
+                                                                 const int32_t* __restrict__ idx, int b,
+                                                                 float* __restrict__ amp) {
+  constexpr int PL = (M + 31) / 32, RW = kGatherRows;
+  static_assert(M % RW == 0, "row groups stay within one position");
+  __shared__ float rows[kGatherWarps][RW][M];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_groups = b * (M / RW);
+  for (int g = blockIdx.x * kGatherWarps + warp; g < n_groups; g += gridDim.x * kGatherWarps) {
+    const int kk = g / (M / RW), er0 = (g % (M / RW)) * RW;
+    const size_t k = (size_t)idx[kk];
+    float v[RW][PL];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      const float* src = d + (k * M + storage_to_freq<M>(er0 + r)) * M;
+#pragma unroll
+      for (int j = 0; j < PL; ++j)
+        if (lane + 32 * j < M) v[r][j] = src[lane + 32 * j];
+    }
+#pragma unroll
+    for (int r = 0; r < RW; ++r)
+#pragma unroll
+      for (int j = 0; j < PL; ++j)
+        if (lane + 32 * j < M) rows[warp][r][lane + 32 * j] = v[r][j];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      float* dst = amp + (k * M + er0 + r) * M;
+#pragma unroll
+      for (int j = 0; j < PL; ++j) {
+        const int ec = lane + 32 * j;
+        if (ec < M) dst[ec] = sqrtf(fmaxf(rows[warp][r][storage_to_freq<M>(ec)], 0.f));
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -1716,15 +1785,33 @@ cudaError_t upload_twiddles() {
 }
 
 cudaError_t launch_amp_prep(const float* d, float* amp, int m, int n_pos, cudaStream_t s) {
-  const size_t total = (size_t)n_pos * m * m;
-  int blocks = (int)((total + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  const size_t rows = (size_t)n_pos * m;
+  int blocks = (int)((rows + 7) / 8);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks == 0) return cudaSuccess;
   switch (m) {
     case 16: k_amp_prep<16><<<blocks, 256, 0, s>>>(d, amp, n_pos); break;
     case 32: k_amp_prep<32><<<blocks, 256, 0, s>>>(d, amp, n_pos); break;
     case 64: k_amp_prep<64><<<blocks, 256, 0, s>>>(d, amp, n_pos); break;
     case 128: k_amp_prep<128><<<blocks, 256, 0, s>>>(d, amp, n_pos); break;
     case 256: k_amp_prep<256><<<blocks, 256, 0, s>>>(d, amp, n_pos); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_amp_gather(const float* d, const int32_t* idx, int b, float* amp, int m, cudaStream_t s) {
+  const int groups = b * (m / kGatherRows);
+  int blocks = (groups + kGatherWarps - 1) / kGatherWarps;
+  if (blocks > kGatherBlocks) blocks = kGatherBlocks;
+  if (blocks == 0) return cudaSuccess;
+  const dim3 th(kGatherWarps * 32);
+  switch (m) {
+    case 16: k_amp_gather<16><<<blocks, th, 0, s>>>(d, idx, b, amp); break;
+    case 32: k_amp_gather<32><<<blocks, th, 0, s>>>(d, idx, b, amp); break;
+    case 64: k_amp_gather<64><<<blocks, th, 0, s>>>(d, idx, b, amp); break;
+    case 128: k_amp_gather<128><<<blocks, th, 0, s>>>(d, idx, b, amp); break;
+    case 256: k_amp_gather<256><<<blocks, th, 0, s>>>(d, idx, b, amp); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
