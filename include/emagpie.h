@@ -207,14 +207,27 @@ emg_status emg_run_epochs(emg_ctx* ctx, int32_t n_epochs, const int32_t* order,
  *   grad_Q Phi = sum_k conj(P_k z) (Q . P_k z - R_k),
  * in the convention d/dRe + i d/dIm (twice the conjugate Wirtinger derivative,
  * the convention PyTorch uses for complex autograd).  R_k is recomputed (no
- * exit waves are stored); positions are processed in chunks of
- * params.minibatch and summed in a fixed order (deterministic).
+ * exit waves are stored); positions are processed in chunks (by default a
+ * multiple of the position clusters that can be resident at once, about 128
+ * positions; see emg_set_gradient_chunk) and summed in a fixed order, so
+ * results repeat bitwise for a given chunk size.  The first call may allocate
+ * the chunk's patch buffers.
  *  object, probe            device complex64 [n_rows][n_cols], [m][m] (read only)
  *  grad_object, grad_probe  device complex64, same shapes, overwritten; either may be NULL
  *  misfit                   host double or NULL (synchronises when not NULL)
  */
 emg_status emg_misfit_gradient(emg_ctx* ctx, const float* object, const float* probe,
                                float* grad_object, float* grad_probe, double* misfit);
+
+/*
+ * Positions per launch of emg_misfit_gradient: 0 (the default) chooses a
+ * multiple of the position clusters that can be resident at once, about 128
+ * positions; n > 0 takes n.  The chunk only
+ * changes speed and the rounding order of the sums.  Synchronises the
+ * context's stream and frees the previous chunk's buffers.  EMG_EINVAL for
+ * n < 0.
+ */
+emg_status emg_set_gradient_chunk(emg_ctx* ctx, int32_t positions);
 
 /* Phi(Q, z) = 1/2 sum_k ||Q . P_k z - R_k||^2 of the bound state (host *out; synchronises). */
 emg_status emg_misfit(emg_ctx* ctx, double* out);

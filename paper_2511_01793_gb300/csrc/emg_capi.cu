@@ -78,6 +78,10 @@ struct emg_ctx {
   float* d_stage_d = nullptr;     // [N][m][m] intensity staging (host input path)
   float2* d_own_object = nullptr; // host-buffer path state
   float2* d_own_probe = nullptr;
+  int grad_chunk_req = 0;         // positions per gradient launch asked for (0: automatic)
+  int grad_chunk = 0;             // positions per gradient launch in use (0: not chosen yet)
+  float2* d_gz = nullptr;         // [grad_chunk][m][m] when it exceeds the minibatch
+  float2* d_gq = nullptr;
   double* h_scalar = nullptr;     // pinned [64]
 
   // kernel timing (emg_set_profiling): CUDA events around each launch, per kernel kind
@@ -244,6 +248,8 @@ void free_all(emg_ctx* c) {
   cudaFree(c->d_stage_d);
   cudaFree(c->d_own_object);
   cudaFree(c->d_own_probe);
+  cudaFree(c->d_gz);
+  cudaFree(c->d_gq);
   if (c->h_scalar) cudaFreeHost(c->h_scalar);
   emg::tc_work_destroy(c->tc);
   c->tc = nullptr;
@@ -1010,7 +1016,27 @@ emg_status emg_misfit_gradient(emg_ctx* c, const float* object, const float* pro
   if (!c) return EMG_EINVAL;
   if (!object || !probe) return fail(c, EMG_EINVAL, "object or probe is NULL");
   DeviceGuard g(c->device);
-  const int N = c->n_pos, B = c->par.minibatch;
+  const int N = c->n_pos;
+  if (c->grad_chunk == 0) {
+    // By default a multiple of the position clusters that can be resident at
+    // once, about 128 positions per launch; the chunking fixes the order of the sums.
+    const int pw = emg::gradient_positions_per_wave(c->m);
+    int chunk = c->grad_chunk_req > 0 ? c->grad_chunk_req : pw > 0 ? pw * ((128 + pw - 1) / pw) : c->par.minibatch;
+    if (chunk > N) chunk = N;
+    if (chunk > c->par.minibatch) {
+      const size_t bytes = (size_t)chunk * c->m * c->m * sizeof(float2);
+      if (cudaMalloc(&c->d_gz, bytes) != cudaSuccess || cudaMalloc(&c->d_gq, bytes) != cudaSuccess) {
+        cudaFree(c->d_gz);
+        c->d_gz = nullptr;
+        cudaGetLastError();
+        return fail(c, EMG_ENOMEM, "cudaMalloc(gradient patches) failed");
+      }
+    }
+    c->grad_chunk = chunk;
+  }
+  const int B = c->grad_chunk;
+  float2* gz = c->d_gz ? c->d_gz : c->d_zt;
+  float2* gq = c->d_gq ? c->d_gq : c->d_qt;
   for (int first = 0; first < N; first += B) {
     const int b = (N - first < B) ? N - first : B;
     emg::GradArgs ga{};
@@ -1021,8 +1047,8 @@ emg_status emg_misfit_gradient(emg_ctx* c, const float* object, const float* pro
     ga.first = first;
     ga.n_rows = c->n_rows;
     ga.n_cols = c->n_cols;
-    ga.gz = c->d_zt;
-    ga.gq = c->d_qt;
+    ga.gz = gz;
+    ga.gq = gq;
     ga.phi = c->d_phi + first;
     cudaError_t e = emg::launch_gradient(c->m, b, ga, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "k_gradc launch");
@@ -1036,8 +1062,8 @@ emg_status emg_misfit_gradient(emg_ctx* c, const float* object, const float* pro
       ra.n_cols = c->n_cols;
       ra.m = c->m;
       ra.accumulate = first > 0;
-      ra.gz = c->d_zt;
-      ra.gq = c->d_qt;
+      ra.gz = gz;
+      ra.gq = gq;
       ra.grad_object = (float2*)grad_object;
       ra.grad_probe = (float2*)grad_probe;
       ra.tiles_x = (c->n_cols + emg::kApplyTile - 1) / emg::kApplyTile;
@@ -1054,6 +1080,19 @@ emg_status emg_misfit_gradient(emg_ctx* c, const float* object, const float* pro
     EMG_CUDA(c, cudaStreamSynchronize(c->stream));
     *misfit = c->h_scalar[0];
   }
+  return EMG_OK;
+}
+
+emg_status emg_set_gradient_chunk(emg_ctx* c, int32_t positions) {
+  if (!c) return EMG_EINVAL;
+  if (positions < 0) return fail(c, EMG_EINVAL, "gradient chunk < 0");
+  DeviceGuard g(c->device);
+  EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  cudaFree(c->d_gz);
+  cudaFree(c->d_gq);
+  c->d_gz = c->d_gq = nullptr;
+  c->grad_chunk_req = positions;
+  c->grad_chunk = 0;
   return EMG_OK;
 }
 

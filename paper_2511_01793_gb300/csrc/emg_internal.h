@@ -124,6 +124,8 @@ struct GradReduceArgs {
 };
 
 cudaError_t launch_gradient(int m, int b, const GradArgs& a, cudaStream_t s);
+// Positions whose gradient clusters are resident on the device at once (0 if unknown).
+int gradient_positions_per_wave(int m);
 cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t s);
 bool step_supported(int m, int levels, int cluster);
 int default_cluster(int m, int levels);

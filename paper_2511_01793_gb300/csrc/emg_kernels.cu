@@ -2096,6 +2096,40 @@ cudaError_t launch_fft2(int m, const float2* in, float2* out, int count, int inv
   EMG_DISPATCH_M(m, (launch_fft2_t<M>(in, out, count, inverse, s)));
 }
 
+template <int M>
+int gradient_wave_t() {
+  constexpr int C = ClusterSize<M>::value;
+  using TL = CTile<M, C>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C * 4096);
+  cfg.blockDim = dim3(TL::NT);
+  cfg.dynamicSmemBytes = TL::smem_elems * sizeof(float2);
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = C;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_gradc<M, C>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+int gradient_positions_per_wave(int m) {
+  switch (m) {
+    case 16: return gradient_wave_t<16>();
+    case 32: return gradient_wave_t<32>();
+    case 64: return gradient_wave_t<64>();
+    case 128: return gradient_wave_t<128>();
+    case 256: return gradient_wave_t<256>();
+    default: return 0;
+  }
+}
+
 cudaError_t launch_gradient(int m, int b, const GradArgs& a, cudaStream_t s) {
   switch (m) {
     case 16: return launch_gradc_t<16>(b, a, s);

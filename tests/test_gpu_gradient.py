@@ -28,11 +28,15 @@ def _gpu_gradient(lib, torch, ctx, z, q):
     return phi, gz.cpu().numpy().astype(np.complex128), gq.cpu().numpy().astype(np.complex128)
 
 
+@pytest.mark.parametrize("chunk", [6, 0])
 @pytest.mark.parametrize("m", [16, 32, 64, 128, 256])
-def test_gradient_matches_the_oracle(lib, torch, m):
+def test_gradient_matches_the_oracle(lib, torch, m, chunk):
+    """16 positions in chunks of 6 (sums over several launches), and in the
+    automatic chunk (one launch here)."""
     case = Case(n=2 * m + 40, m=m, side=4, noise_peak=1e4, seed=40 + m)
-    p = oracle_params(minibatch=6)          # 20 positions in chunks of 6
+    p = oracle_params(minibatch=6)
     ctx = make_context(lib, case, p)
+    lib.emg_set_gradient_chunk(ctx.ctx, chunk)
     phi, gz, gq = _gpu_gradient(lib, torch, ctx, case.z0, case.q0)
     ctx.close()
     phi_o, gz_o, gq_o = O.misfit_gradients(case.q0.astype(np.complex128), case.z0.astype(np.complex128),
