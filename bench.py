@@ -744,7 +744,7 @@ def run_gpu_batch(args, world, rank, local):
     emg.load()
     probs = batch_problems()
     stream = torch.cuda.Stream()
-    ctxs, total_pos, alg_bytes, tiles = [], 0, 0, {}
+    ctxs, total_pos, alg_bytes, tiles, batches = [], 0, 0, {}, {}
     gen = torch.Generator(device="cuda")
     with torch.cuda.stream(stream):
         for pr in probs:
@@ -769,8 +769,11 @@ def run_gpu_batch(args, world, rank, local):
                               probe=torch.from_numpy(synth.blur_probe(q_true, 2.0).astype(np.complex64)),
                               stream=stream)
             emg.emg_normalize_probe(ctx.ctx)
-            chosen, _ = emg.emg_autotune(ctx.ctx)
-            tiles[f"m{m}"] = tiles.get(f"m{m}", []) + [chosen]
+            # B by the largest misfit decrease per second over two trial epochs, then the tiling
+            tuned = emg.emg_autotune_search(ctx.ctx, minibatch=sorted({min(b, N) for b in (16, 32, 64)}),
+                                            trial_epochs=2, tune_tiling=True, allow_atomic=False)
+            tiles[f"m{m}"] = tiles.get(f"m{m}", []) + [tuned["cluster"]]
+            batches[f"m{m}"] = batches.get(f"m{m}", []) + [tuned["minibatch"]]
             del ctx.intensity
             ctxs.append(ctx)
             total_pos += N
@@ -803,7 +806,10 @@ def run_gpu_batch(args, world, rank, local):
         "config": {"workload": f"batch64: {len(probs)} problems, {total_pos} positions per epoch, object "
                                "256-1024, probe 64-256, 2-3 levels, one graph launch per epoch",
                    "l2": f"inputs {alg_bytes / 2.5e9:.1f} GB of amplitudes and patches, larger than L2",
-                   "tiling_chosen": {k: sorted(set(v)) for k, v in tiles.items()}},
+                   "tiling_chosen": {k: sorted(set(v)) for k, v in tiles.items()},
+                   "minibatch_chosen": {k: {str(b): v.count(b) for b in sorted(set(v))} for k, v in batches.items()},
+                   "autotune": "per problem: B from {16, 32, 64} by misfit decrease per second over two trial "
+                               "epochs, then the FFT tiling by epoch time; deterministic scatter"},
         "e2e": None, "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 5), "peak_source": peak_kind, "traffic": None,

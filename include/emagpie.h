@@ -331,6 +331,52 @@ emg_status emg_set_cluster(emg_ctx* ctx, int32_t cluster);
 emg_status emg_autotune(emg_ctx* ctx, int32_t* chosen, double* ms_per_minibatch);
 
 /*
+ * Minibatch size B (1..n_pos) after creation.  B is part of the method: it
+ * sets how many positions share one snapshot and one combine (reading of the
+ * minibatch combine), so it changes results, not only speed.  Synchronises;
+ * grows the per-minibatch buffers when B exceeds every earlier size.
+ * EMG_EINVAL outside 1..n_pos, EMG_ENOMEM when the buffers cannot grow (the
+ * context keeps its previous B).
+ */
+emg_status emg_set_minibatch(emg_ctx* ctx, int32_t minibatch);
+
+/*
+ * Object scatter mode after creation (EMG_SCATTER_DETERMINISTIC or
+ * EMG_SCATTER_ATOMIC; see emg_params.scatter).  Synchronises; allocates the
+ * atomic accumulators on first use.  EMG_EINVAL for an unknown mode or for the
+ * atomic weighted mean with w_eps = 0.
+ */
+emg_status emg_set_scatter(emg_ctx* ctx, int32_t scatter);
+
+typedef struct {
+  const int32_t* minibatch;  /* host [n_minibatch]: candidate B values (1..n_pos) */
+  int32_t n_minibatch;       /* 0: keep the context's B */
+  int32_t trial_epochs;      /* >= 1: epochs each B candidate runs */
+  int32_t tune_tiling;       /* 1: also choose the FFT tiling (emg_set_cluster) */
+  int32_t allow_atomic;      /* 1: also try the other scatter mode; the atomic one
+                                is not bitwise repeatable */
+} emg_tune_request;
+
+typedef struct {
+  int32_t minibatch, cluster, scatter;  /* the configuration now set on the context */
+  double ms_per_epoch;                  /* its device time per epoch */
+  double misfit_rate;                   /* ln(Phi_0 / Phi_end) per second in the B trial */
+} emg_tune_result;
+
+/*
+ * Autotuner over B, the FFT tiling and the scatter mode.  Every trial starts
+ * from a private copy of the bound state at the context's epoch counter; the
+ * bound state and the counter are left untouched.  B: each candidate runs
+ * trial_epochs epochs, and the one with the largest misfit decrease per
+ * second, ln(Phi_0 / Phi_end) / t, wins (B changes the iterates, so speed
+ * alone cannot choose it).  Tiling and scatter mode: the fastest epoch at that
+ * B (the tiling leaves results unchanged; the scatter modes differ by
+ * rounding).  The winners are set on the context and returned in *result.
+ * Synchronises.  EMG_EINVAL for invalid requests.
+ */
+emg_status emg_autotune_search(emg_ctx* ctx, const emg_tune_request* request, emg_tune_result* result);
+
+/*
  * Batches of independent reconstructions (problems of different object, probe
  * and scan sizes).  emg_batch_create groups `count` contexts on one device,
  * each with its state bound; the contexts stay owned by the caller and must

@@ -27,7 +27,8 @@ __all__ = [
     "emg_step_minibatch", "emg_position_stats", "emg_set_verify", "emg_run_epochs", "emg_misfit",
     "emg_set_epoch", "emg_schedule_permutation", "emg_stopping_epoch", "emg_run_until", "emg_reconstruct_host",
     "emg_simulate_intensity", "emg_fft2", "emg_dft2_bf16x3", "emg_step_minibatch_noalloc", "emg_misfit_gradient",
-    "emg_set_cluster", "emg_set_gradient_chunk", "emg_autotune", "emg_batch_create", "emg_batch_run_epochs", "emg_batch_destroy",
+    "emg_set_cluster", "emg_set_gradient_chunk", "emg_autotune", "emg_set_minibatch", "emg_set_scatter",
+    "emg_autotune_search", "EmgTuneRequest", "EmgTuneResult", "emg_batch_create", "emg_batch_run_epochs", "emg_batch_destroy",
     "emg_set_profiling",
     "emg_profile_read",
     "emg_last_error", "emg_destroy", "Context",
@@ -64,6 +65,16 @@ class EmgParams(ctypes.Structure):
 _lib: Optional[ctypes.CDLL] = None
 
 _I32P = ctypes.POINTER(ctypes.c_int32)
+class EmgTuneRequest(ctypes.Structure):
+    _fields_ = [("minibatch", ctypes.c_void_p), ("n_minibatch", ctypes.c_int32), ("trial_epochs", ctypes.c_int32),
+                ("tune_tiling", ctypes.c_int32), ("allow_atomic", ctypes.c_int32)]
+
+
+class EmgTuneResult(ctypes.Structure):
+    _fields_ = [("minibatch", ctypes.c_int32), ("cluster", ctypes.c_int32), ("scatter", ctypes.c_int32),
+                ("ms_per_epoch", ctypes.c_double), ("misfit_rate", ctypes.c_double)]
+
+
 _F64P = ctypes.POINTER(ctypes.c_double)
 _VP = ctypes.c_void_p
 _SIGS = {
@@ -97,6 +108,9 @@ _SIGS = {
     "emg_set_cluster": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "emg_set_gradient_chunk": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "emg_autotune": (ctypes.c_int, [_VP, _I32P, _F64P]),
+    "emg_set_minibatch": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "emg_set_scatter": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "emg_autotune_search": (ctypes.c_int, [_VP, ctypes.POINTER(EmgTuneRequest), ctypes.POINTER(EmgTuneResult)]),
     "emg_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int32]),
     "emg_batch_run_epochs": (ctypes.c_int, [_VP, ctypes.c_int32, _VP]),
     "emg_batch_destroy": (None, [_VP]),
@@ -324,6 +338,27 @@ def emg_set_gradient_chunk(ctx: int, positions: int) -> None:
 
 def emg_set_cluster(ctx: int, cluster: int) -> None:
     _check(load().emg_set_cluster(ctx, cluster), "emg_set_cluster", ctx)
+
+
+def emg_set_minibatch(ctx: int, minibatch: int) -> None:
+    _check(load().emg_set_minibatch(ctx, minibatch), "emg_set_minibatch", ctx)
+
+
+def emg_set_scatter(ctx: int, scatter: int) -> None:
+    _check(load().emg_set_scatter(ctx, scatter), "emg_set_scatter", ctx)
+
+
+def emg_autotune_search(ctx: int, minibatch=(), trial_epochs: int = 2, tune_tiling: bool = True,
+                        allow_atomic: bool = False) -> dict:
+    """Chooses B (largest misfit decrease per second), then the FFT tiling and
+    optionally the scatter mode; sets them on the context and returns them."""
+    cands = np.ascontiguousarray(list(minibatch), dtype=np.int32)
+    req = EmgTuneRequest(cands.ctypes.data if len(cands) else None, len(cands), trial_epochs,
+                         int(tune_tiling), int(allow_atomic))
+    res = EmgTuneResult()
+    _check(load().emg_autotune_search(ctx, ctypes.byref(req), ctypes.byref(res)), "emg_autotune_search", ctx)
+    return {"minibatch": res.minibatch, "cluster": res.cluster, "scatter": res.scatter,
+            "ms_per_epoch": res.ms_per_epoch, "misfit_rate": res.misfit_rate}
 
 
 def emg_autotune(ctx: int):

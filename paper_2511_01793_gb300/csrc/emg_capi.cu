@@ -1,6 +1,8 @@
 // C ABI of the eMAGPIE hot path: context, validation, scratch ownership and
 // the minibatch / epoch drivers (Sec. 3 stochastic sweep of arXiv 2511.01793).
 #include <math.h>
+#include <algorithm>
+#include <cmath>
 #include <stdlib.h>
 #include <string.h>
 
@@ -78,6 +80,7 @@ struct emg_ctx {
   float* d_stage_d = nullptr;     // [N][m][m] intensity staging (host input path)
   float2* d_own_object = nullptr; // host-buffer path state
   float2* d_own_probe = nullptr;
+  int cap_minibatch = 0;          // minibatch capacity of the per-minibatch buffers
   int grad_chunk_req = 0;         // positions per gradient launch asked for (0: automatic)
   int grad_chunk = 0;             // positions per gradient launch in use (0: not chosen yet)
   float2* d_gz = nullptr;         // [grad_chunk][m][m] when it exceeds the minibatch
@@ -411,8 +414,9 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   sa.phi_after = c->d_phi_after;
   sa.combine = c->par.combine;
   sa.w_eps = c->par.w_eps;
-  sa.s_num = c->d_snum;
-  sa.s_den = c->d_sden;
+  const bool atomic = c->par.scatter == EMG_SCATTER_ATOMIC;
+  sa.s_num = atomic ? c->d_snum : nullptr;
+  sa.s_den = atomic ? c->d_sden : nullptr;
   if (c->tc) {
     emg::TcStepArgs ta{};
     ta.object = c->object;
@@ -459,8 +463,8 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   aa.mq_next = c->d_mq + ((seq + 1) & 1);
   aa.tiles_x = (c->n_cols + emg::kApplyTile - 1) / emg::kApplyTile;
   aa.tiles_y = (c->n_rows + emg::kApplyTile - 1) / emg::kApplyTile;
-  aa.s_num = c->d_snum;
-  aa.s_den = c->d_sden;
+  aa.s_num = atomic ? c->d_snum : nullptr;
+  aa.s_den = atomic ? c->d_sden : nullptr;
   {
     LaunchMark mk(c, kKindApply);
     e = emg::launch_apply(aa, strm);
@@ -541,6 +545,92 @@ emg_status ensure_epoch_graph(emg_ctx* c, EpochGraph& G, const float* src) {
   G.verify = c->verify;
   G.cluster = c->cluster;
   G.src = src;
+  return EMG_OK;
+}
+
+// Drops the captured epochs (they hold the buffers and settings they were captured with).
+void drop_graphs(emg_ctx* c) {
+  for (EpochGraph* G : {&c->graph, &c->sgraph}) {
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    *G = EpochGraph();
+  }
+}
+
+emg_status set_minibatch_impl(emg_ctx* c, int32_t B) {
+  if (B < 1 || B > c->n_pos) return fail(c, EMG_EINVAL, "minibatch must be in 1..n_pos");
+  if (B == c->par.minibatch) return EMG_OK;
+  EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (B > c->cap_minibatch) {
+    const size_t mm = (size_t)c->m * c->m;
+    float2 *zt = nullptr, *qt = nullptr, *r = nullptr;
+    float* mu = nullptr;
+    double *after = nullptr, *part = nullptr;
+    emg::TcWork* tc = nullptr;
+    bool ok = !dmalloc(&zt, (size_t)B * mm) && !dmalloc(&qt, (size_t)B * mm) && !dmalloc(&mu, (size_t)B) &&
+              !dmalloc(&after, (size_t)B);
+    if (ok && c->tc)
+      ok = emg::tc_work_create(&tc, c->m, B) == cudaSuccess && !dmalloc(&r, (size_t)B * mm) &&
+           !dmalloc(&part, (size_t)B * emg::tc_tiles_per_position(c->m));
+    if (!ok) {
+      cudaFree(zt);
+      cudaFree(qt);
+      cudaFree(mu);
+      cudaFree(after);
+      cudaFree(r);
+      cudaFree(part);
+      if (tc) emg::tc_work_destroy(tc);
+      cudaGetLastError();
+      return fail(c, EMG_ENOMEM, "minibatch buffers");
+    }
+    cudaFree(c->d_zt);
+    cudaFree(c->d_qt);
+    cudaFree(c->d_mu);
+    cudaFree(c->d_phi_after);
+    c->d_zt = zt;
+    c->d_qt = qt;
+    c->d_mu = mu;
+    c->d_phi_after = after;
+    if (c->tc) {
+      emg::tc_work_destroy(c->tc);
+      cudaFree(c->d_tc_r);
+      cudaFree(c->d_tc_part);
+      c->tc = tc;
+      c->d_tc_r = r;
+      c->d_tc_part = part;
+    }
+    c->cap_minibatch = B;
+  }
+  EMG_CUDA(c, cudaMemsetAsync(c->d_phi_after, 0xff, (size_t)c->cap_minibatch * sizeof(double), c->stream));
+  c->par.minibatch = B;
+  // the gradient may have used the minibatch buffers for its patches
+  cudaFree(c->d_gz);
+  cudaFree(c->d_gq);
+  c->d_gz = c->d_gq = nullptr;
+  c->grad_chunk = 0;
+  drop_graphs(c);
+  return EMG_OK;
+}
+
+emg_status set_scatter_impl(emg_ctx* c, int32_t mode) {
+  if (mode != EMG_SCATTER_DETERMINISTIC && mode != EMG_SCATTER_ATOMIC) return fail(c, EMG_EINVAL, "unknown scatter mode");
+  if (mode == EMG_SCATTER_ATOMIC && c->par.combine == EMG_COMBINE_WAVG && !(c->par.w_eps > 0.f))
+    return fail(c, EMG_EINVAL, "the atomic weighted-mean scatter needs w_eps > 0 (coverage is read from the weights)");
+  if (mode == c->par.scatter) return EMG_OK;
+  EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (mode == EMG_SCATTER_ATOMIC && !c->d_snum) {
+    const size_t npx = (size_t)c->n_rows * c->n_cols;
+    if (dmalloc(&c->d_snum, npx) || dmalloc(&c->d_sden, npx)) {
+      cudaFree(c->d_snum);
+      c->d_snum = nullptr;
+      c->d_sden = nullptr;
+      cudaGetLastError();
+      return fail(c, EMG_ENOMEM, "atomic scatter accumulators");
+    }
+    EMG_CUDA(c, cudaMemsetAsync(c->d_snum, 0, npx * sizeof(float2), c->stream));
+    EMG_CUDA(c, cudaMemsetAsync(c->d_sden, 0, npx * sizeof(float), c->stream));
+  }
+  c->par.scatter = mode;
+  drop_graphs(c);
   return EMG_OK;
 }
 
@@ -686,6 +776,42 @@ emg_status set_intensity_impl(emg_ctx* c, const float* intensity) {
   return EMG_OK;
 }
 
+// Phi of the bound state (FP64 sum), synchronising.
+emg_status misfit_now(emg_ctx* c, double* out) {
+  cudaError_t e = emg::launch_misfit(c->m, c->object, c->probe, c->d_pos, c->d_amp, c->n_rows, c->n_cols,
+                                     c->n_pos, c->d_partial, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_misfit launch");
+  e = emg::launch_sum(c->d_partial, c->n_pos, 1.0, c->d_scalar, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_sum launch");
+  EMG_CUDA(c, cudaMemcpyAsync(c->h_scalar, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  *out = c->h_scalar[0];
+  return EMG_OK;
+}
+
+// One trial of the search: `epochs` epochs from the saved state (copied into
+// the private buffers, which are bound), after one untimed epoch that captures
+// the graph.  Returns the device time and the misfit at the end.
+emg_status tune_trial(emg_ctx* c, const float2* o0, const float2* p0, float2* tz, float2* tq, int64_t epoch0,
+                      int epochs, cudaEvent_t e0, cudaEvent_t e1, double* ms, double* phi_end) {
+  const size_t nz = (size_t)c->n_rows * c->n_cols, nq = (size_t)c->m * c->m;
+  emg_status st = EMG_OK;
+  for (int pass = 0; pass < 2 && st == EMG_OK; ++pass) {
+    EMG_CUDA(c, cudaMemcpyAsync(tz, o0, nz * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+    EMG_CUDA(c, cudaMemcpyAsync(tq, p0, nq * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+    c->epoch = epoch0;
+    if (pass == 1) EMG_CUDA(c, cudaEventRecord(e0, c->stream));
+    st = run_epochs_impl(c, pass == 0 ? 1 : epochs, nullptr, nullptr, nullptr);
+    if (pass == 1 && st == EMG_OK) EMG_CUDA(c, cudaEventRecord(e1, c->stream));
+  }
+  if (st != EMG_OK) return st;
+  EMG_CUDA(c, cudaEventSynchronize(e1));
+  float f = 0.f;
+  EMG_CUDA(c, cudaEventElapsedTime(&f, e0, e1));
+  *ms = f;
+  return misfit_now(c, phi_end);
+}
+
 }  // namespace
 
 extern "C" {
@@ -785,6 +911,7 @@ emg_status emg_create(emg_ctx** out, const emg_problem* pr, const emg_params* pa
     return bail(EMG_ECUDA);
   if (cudaMemsetAsync(c->d_phi_after, 0xff, (size_t)B * sizeof(double), c->stream) != cudaSuccess)
     return bail(EMG_ECUDA);
+  c->cap_minibatch = B;
   if (set_intensity_impl(c, pr->intensity) != EMG_OK) return bail(EMG_ECUDA);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(EMG_ECUDA);
   *out = c;
@@ -1104,6 +1231,119 @@ emg_status emg_set_cluster(emg_ctx* c, int32_t cluster) {
   return EMG_OK;
 }
 
+emg_status emg_set_minibatch(emg_ctx* c, int32_t minibatch) {
+  if (!c) return EMG_EINVAL;
+  DeviceGuard g(c->device);
+  return set_minibatch_impl(c, minibatch);
+}
+
+emg_status emg_set_scatter(emg_ctx* c, int32_t scatter) {
+  if (!c) return EMG_EINVAL;
+  DeviceGuard g(c->device);
+  return set_scatter_impl(c, scatter);
+}
+
+emg_status emg_autotune_search(emg_ctx* c, const emg_tune_request* req, emg_tune_result* res) {
+  if (!c) return EMG_EINVAL;
+  if (!req || !res) return fail(c, EMG_EINVAL, "request or result is NULL");
+  if (req->n_minibatch < 0 || (req->n_minibatch > 0 && !req->minibatch) || req->trial_epochs < 1)
+    return fail(c, EMG_EINVAL, "minibatch candidates or trial epochs invalid");
+  for (int i = 0; i < req->n_minibatch; ++i)
+    if (req->minibatch[i] < 1 || req->minibatch[i] > c->n_pos)
+      return fail(c, EMG_EINVAL, "minibatch candidate outside 1..n_pos");
+  if (req->allow_atomic && c->par.combine == EMG_COMBINE_WAVG && !(c->par.w_eps > 0.f))
+    return fail(c, EMG_EINVAL, "the atomic weighted-mean scatter needs w_eps > 0");
+  emg_status st = check_bound(c);
+  if (st != EMG_OK) return st;
+  DeviceGuard g(c->device);
+  const size_t nz = (size_t)c->n_rows * c->n_cols, nq = (size_t)c->m * c->m;
+  float2 *tz = nullptr, *tq = nullptr;
+  if (cudaMalloc(&tz, nz * sizeof(float2)) != cudaSuccess || cudaMalloc(&tq, nq * sizeof(float2)) != cudaSuccess) {
+    cudaFree(tz);
+    cudaGetLastError();
+    return fail(c, EMG_ENOMEM, "autotune scratch");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float2* keep_o = c->object;
+  float2* keep_p = c->probe;
+  const int64_t keep_epoch = c->epoch;
+  const int keep_profile = c->profile;
+  int64_t keep_launches[kKinds];
+  for (int i = 0; i < kKinds; ++i) keep_launches[i] = c->launches[i];
+  c->profile = 0;
+  double phi0 = 0.0;
+  st = misfit_now(c, &phi0);
+  c->object = tz;
+  c->probe = tq;
+  // 1. B: the largest misfit decrease per second, ln(Phi_0 / Phi_end) / t
+  int best_b = c->par.minibatch;
+  double best_rate = -1e300, best_ms = 0.0;
+  std::vector<int32_t> cands(req->minibatch, req->minibatch + req->n_minibatch);
+  if (cands.empty()) cands.push_back(c->par.minibatch);
+  for (int32_t b : cands) {
+    if (st != EMG_OK) break;
+    if ((st = set_minibatch_impl(c, b)) != EMG_OK) break;
+    double ms = 0.0, phi = 0.0;
+    if ((st = tune_trial(c, keep_o, keep_p, tz, tq, keep_epoch, req->trial_epochs, e0, e1, &ms, &phi)) != EMG_OK)
+      break;
+    const double rate = phi > 0.0 && phi0 > 0.0 ? std::log(phi0 / phi) / (ms * 1e-3) : (phi0 > 0.0 ? 1e300 : 0.0);
+    if (rate > best_rate) {
+      best_rate = rate;
+      best_b = b;
+      best_ms = ms / req->trial_epochs;
+    }
+  }
+  if (st == EMG_OK) st = set_minibatch_impl(c, best_b);
+  // 2. the FFT tiling at that B: time per epoch (results do not depend on it)
+  int best_cluster = c->cluster;
+  if (st == EMG_OK && req->tune_tiling) {
+    double t_best = 1e300;
+    for (int cand : {1, 2, 4, 8}) {
+      if (!emg::step_supported(c->m, c->par.levels, cand)) continue;
+      c->cluster = cand;
+      double ms = 0.0, phi = 0.0;
+      if ((st = tune_trial(c, keep_o, keep_p, tz, tq, keep_epoch, 1, e0, e1, &ms, &phi)) != EMG_OK) break;
+      if (ms < t_best) {
+        t_best = ms;
+        best_cluster = cand;
+      }
+    }
+    c->cluster = best_cluster;
+    if (st == EMG_OK) best_ms = t_best;
+  }
+  // 3. the scatter mode, when non-repeatable sums are allowed
+  if (st == EMG_OK && req->allow_atomic) {
+    const int keep_scatter = c->par.scatter;
+    const int other = keep_scatter == EMG_SCATTER_ATOMIC ? EMG_SCATTER_DETERMINISTIC : EMG_SCATTER_ATOMIC;
+    double ms_keep = 0.0, ms_other = 0.0, phi = 0.0;
+    st = tune_trial(c, keep_o, keep_p, tz, tq, keep_epoch, 1, e0, e1, &ms_keep, &phi);
+    if (st == EMG_OK) st = set_scatter_impl(c, other);
+    if (st == EMG_OK) st = tune_trial(c, keep_o, keep_p, tz, tq, keep_epoch, 1, e0, e1, &ms_other, &phi);
+    if (st == EMG_OK && ms_other >= ms_keep) st = set_scatter_impl(c, keep_scatter);
+    if (st == EMG_OK) best_ms = std::min(ms_keep, ms_other);
+  }
+  cudaStreamSynchronize(c->stream);
+  c->object = keep_o;
+  c->probe = keep_p;
+  c->epoch = keep_epoch;
+  c->profile = keep_profile;
+  for (int i = 0; i < kKinds; ++i) c->launches[i] = keep_launches[i];
+  drop_graphs(c);  // captured with the private buffers
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(tz);
+  cudaFree(tq);
+  if (st != EMG_OK) return st;
+  res->minibatch = c->par.minibatch;
+  res->cluster = c->cluster;
+  res->scatter = c->par.scatter;
+  res->ms_per_epoch = best_ms;
+  res->misfit_rate = best_rate;
+  return EMG_OK;
+}
+
 emg_status emg_autotune(emg_ctx* c, int32_t* chosen, double* ms_per_minibatch) {
   if (!c) return EMG_EINVAL;
   emg_status st = check_bound(c);
@@ -1225,7 +1465,9 @@ emg_status emg_batch_run_epochs(emg_batch* b, int32_t n_epochs, emg_stream_t str
     dst[i] = c->d_epoch_order;
     ns[i] = N;
     key.insert(key.end(), {c->d_orders, c->object, c->probe, (const void*)(intptr_t)c->cluster,
-                           (const void*)(intptr_t)c->verify, (const void*)(intptr_t)c->profile});
+                           (const void*)(intptr_t)c->verify, (const void*)(intptr_t)c->profile,
+                           (const void*)(intptr_t)c->par.minibatch, (const void*)(intptr_t)c->par.scatter,
+                           c->d_zt});
   }
   if (cudaMemcpyAsync(b->d_src, src.data(), K * sizeof(int32_t*), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(b->d_dst, dst.data(), K * sizeof(int32_t*), cudaMemcpyHostToDevice, s) != cudaSuccess ||

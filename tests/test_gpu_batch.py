@@ -3,6 +3,7 @@ tiling (CTAs per position) and its autotuner."""
 import numpy as np
 import pytest
 
+import oracle as O
 from emg_cases import Case, make_context, oracle_params, rel_err, state
 
 pytestmark = pytest.mark.gpu
@@ -152,3 +153,102 @@ def test_autotune_on_the_tensor_core_path_keeps_results(lib, torch):
     assert np.array_equal(zt, zp) and np.array_equal(qt, qp)      # tilings agree bitwise for m >= 64
     tuned.close()
     plain.close()
+
+
+def _epoch_by_hand(lib, ctx, order, b):
+    """One epoch as explicit minibatches of b positions (the last one shorter)."""
+    for i in range(0, len(order), b):
+        lib.emg_step_minibatch(ctx.ctx, order[i:i + b])
+
+
+@pytest.mark.parametrize("m,dft", [(32, 0), (128, 0), (128, 1)])
+def test_minibatch_can_change_after_creation(lib, torch, m, dft):
+    """An epoch at B = 4, then B grows to 7 (new buffers, a new captured epoch)
+    and shrinks to 3: equal bitwise to the same minibatches stepped by hand on
+    a context created with the largest B."""
+    case = Case(n=2 * m + 40, m=m, side=5, noise_peak=1e4, seed=80 + m + dft)
+    p = oracle_params(minibatch=4, levels=2, prolong="bilinear")
+    orders = np.stack([O.schedule_permutation(9, e, case.n_pos) for e in range(3)]).astype(np.int32)
+    c1 = make_context(lib, case, p, seed=9, dft=dft)
+    lib.emg_run_epochs(c1.ctx, 1, orders[0:1])
+    lib.emg_set_minibatch(c1.ctx, 7)
+    lib.emg_run_epochs(c1.ctx, 1, orders[1:2])
+    lib.emg_set_minibatch(c1.ctx, 3)
+    lib.emg_run_epochs(c1.ctx, 1, orders[2:3])
+    p7 = oracle_params(minibatch=7, levels=2, prolong="bilinear")
+    c2 = make_context(lib, case, p7, seed=9, dft=dft)
+    for order, b in zip(orders, (4, 7, 3)):
+        _epoch_by_hand(lib, c2, order, b)
+    z1, q1 = state(c1)
+    z2, q2 = state(c2)
+    assert np.array_equal(z1, z2) and np.array_equal(q1, q2)
+    with pytest.raises(lib.EmgError):
+        lib.emg_set_minibatch(c1.ctx, 0)
+    with pytest.raises(lib.EmgError):
+        lib.emg_set_minibatch(c1.ctx, case.n_pos + 1)
+    c1.close()
+    c2.close()
+
+
+def test_scatter_mode_can_change_after_creation(lib, torch):
+    """Deterministic -> atomic equals an atomic context up to rounding; back to
+    deterministic equals a deterministic context bitwise."""
+    m = 64
+    case = Case(n=2 * m + 40, m=m, side=4, noise_peak=1e4, seed=91)
+    p = oracle_params(minibatch=5, levels=2, prolong="bilinear")
+    det = make_context(lib, case, p, seed=4)
+    lib.emg_run_epochs(det.ctx, 2)
+    ato = make_context(lib, case, p, seed=4, scatter=1)
+    lib.emg_run_epochs(ato.ctx, 2)
+    c = make_context(lib, case, p, seed=4)
+    lib.emg_run_epochs(c.ctx, 1)                      # captures a deterministic epoch first
+    lib.emg_set_scatter(c.ctx, lib.EMG_SCATTER_ATOMIC)
+    lib.emg_run_epochs(c.ctx, 1)
+    z, q = state(c)
+    c1 = make_context(lib, case, p, seed=4)
+    lib.emg_run_epochs(c1.ctx, 1)
+    lib.emg_set_scatter(c1.ctx, lib.EMG_SCATTER_ATOMIC)
+    lib.emg_set_scatter(c1.ctx, lib.EMG_SCATTER_DETERMINISTIC)
+    lib.emg_run_epochs(c1.ctx, 1)
+    zd, qd = state(det)
+    za, qa = state(ato)
+    z1, q1 = state(c1)
+    assert rel_err(z, zd) <= 1e-5 and rel_err(q, qd) <= 1e-5 and rel_err(z, za) <= 1e-5
+    assert np.array_equal(z1, zd) and np.array_equal(q1, qd)
+    with pytest.raises(lib.EmgError):
+        lib.emg_set_scatter(c1.ctx, 2)
+    for x in (det, ato, c, c1):
+        x.close()
+
+
+def test_autotune_search_chooses_b_tiling_and_scatter(lib, torch):
+    """The search leaves the bound state and the epoch counter alone, returns a
+    candidate B with a positive misfit rate, and the context then runs exactly
+    as one created with the chosen settings."""
+    m = 64
+    case = Case(n=2 * m + 72, m=m, side=6, noise_peak=1e5, seed=93)
+    p = oracle_params(minibatch=8, levels=2, prolong="bilinear")
+    c = make_context(lib, case, p, seed=6)
+    z0, q0 = state(c)
+    res = lib.emg_autotune_search(c.ctx, minibatch=(4, 12, 36), trial_epochs=2, tune_tiling=True,
+                                  allow_atomic=False)
+    z_after, q_after = state(c)
+    assert np.array_equal(z0, z_after) and np.array_equal(q0, q_after)
+    assert res["minibatch"] in (4, 12, 36) and res["cluster"] in (2, 4) and res["scatter"] == 0
+    assert res["misfit_rate"] > 0 and res["ms_per_epoch"] > 0
+    lib.emg_run_epochs(c.ctx, 2)
+    pb = oracle_params(minibatch=res["minibatch"], levels=2, prolong="bilinear")
+    ref = make_context(lib, case, pb, seed=6)
+    lib.emg_set_cluster(ref.ctx, res["cluster"])
+    lib.emg_run_epochs(ref.ctx, 2)
+    z1, q1 = state(c)
+    z2, q2 = state(ref)
+    assert np.array_equal(z1, z2) and np.array_equal(q1, q2)
+    res2 = lib.emg_autotune_search(c.ctx, minibatch=(), trial_epochs=1, tune_tiling=False, allow_atomic=True)
+    assert res2["minibatch"] == res["minibatch"] and res2["scatter"] in (0, 1)
+    with pytest.raises(lib.EmgError):
+        lib.emg_autotune_search(c.ctx, minibatch=(0,))
+    with pytest.raises(lib.EmgError):
+        lib.emg_autotune_search(c.ctx, minibatch=(4,), trial_epochs=0)
+    c.close()
+    ref.close()
