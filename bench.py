@@ -234,6 +234,54 @@ def cpu_oracle_sample(w, d, seconds: float):
     return done / dt, done, dt
 
 
+def _oracle_process(name, path, seconds, barrier, out):
+    """One independent oracle process: the bounded sample on intensities read
+    from `path`, timed from a barrier shared with the other processes."""
+    w = synth.make_workload(name)
+    d = np.load(path)
+    barrier.wait(timeout=300)
+    _, done, dt = cpu_oracle_sample(w, d, seconds)
+    out.put((done, dt))
+
+
+def cpu_oracle_all_cores(w, d, seconds: float):
+    """The same sample in one spawned process per host core (the oracle itself is
+    single-threaded): positions of all processes / the longest process's time.
+    Returns None if a process fails or does not report in time."""
+    import multiprocessing as mp
+    import queue
+
+    procs = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    res = []
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "d.npy")
+        np.save(path, d)
+        barrier, out = ctx.Barrier(procs), ctx.Queue()
+        workers = [ctx.Process(target=_oracle_process, args=(w.name, path, seconds, barrier, out))
+                   for _ in range(procs)]
+        for p in workers:
+            p.start()
+        deadline = time.monotonic() + seconds + 600
+        try:
+            while len(res) < procs and time.monotonic() < deadline:
+                try:
+                    res.append(out.get(timeout=5))
+                except queue.Empty:
+                    if any(p.exitcode not in (None, 0) for p in workers):
+                        break
+        finally:
+            for p in workers:
+                if p.is_alive() and len(res) < procs:
+                    p.terminate()
+                p.join(timeout=60)
+    if len(res) < procs:
+        return None
+    done = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    return done / dt, done, dt, procs
+
+
 def host_intensities(w, rank: int):
     """Noise-free intensities from the library's forward model, Poisson-sampled on the host."""
     import torch
@@ -434,6 +482,13 @@ def run_gpu(args, world, rank, local):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{done} positions ({math.ceil(done / B)} minibatches of "
                                           f"{B}) from the initial state, {dt:.1f} s single-thread FP64"}
+        par = cpu_oracle_all_cores(w, d, args.cpu_seconds)
+        if par is not None:
+            rate_all, done_all, dt_all, procs = par
+            line["cpu_baseline"]["all_cores"] = {
+                "value": rate_all, "unit": UNIT, "cores": procs,
+                "sample": f"{procs} independent oracle processes (spawned), each on the sample above; "
+                          f"{done_all} positions in {dt_all:.1f} s"}
     print(json.dumps(line), flush=True)
     ctx.close()
 
