@@ -166,7 +166,8 @@ emg_status emg_normalize_probe(emg_ctx* ctx);
 
 /*
  * One minibatch: positions idx[0..b-1] (host int32, each in [0, n_pos)),
- * 1 <= b <= params.minibatch.  Updates the bound object and probe.
+ * 1 <= b <= the context's minibatch size (params.minibatch, or the last
+ * emg_set_minibatch).  Updates the bound object and probe.
  * If sampled_misfit (host) is not NULL it receives sum_k Phi_k at the
  * snapshot, Phi_k = 1/2 ||Q . z_k - R_k||^2 (Eq. exit_misfit), and the call
  * synchronises.
@@ -190,7 +191,7 @@ emg_status emg_set_verify(emg_ctx* ctx, int32_t verify);
  * permutation of 0..n_pos-1, or NULL to draw the permutation of epoch e from
  * emg_schedule_permutation(params.seed, e, n_pos) where e counts the epochs
  * this context has run (see emg_set_epoch).  Each epoch is cut into
- * consecutive minibatches of params.minibatch positions (the last may be
+ * consecutive minibatches of the context's minibatch size (the last may be
  * shorter).  running_misfit (host [n_epochs] or NULL) receives the sum over
  * the epoch of the sampled Phi_k; misfit (host [n_epochs] or NULL) receives
  * Phi(Q, z) at the end of each epoch from a separate forward pass.  The call
