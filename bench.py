@@ -103,11 +103,12 @@ def step_flops_per_position(m: int, levels: int) -> float:
     return 10.0 * m * m * math.log2(m * m) + 100.0 * m * m * sum(4.0 ** -l for l in range(levels))
 
 
-def recorded_traffic():
-    """DRAM bytes per step-kernel launch from the committed ncu summary, if still current.
+def recorded_counter(name: str = "dram_bytes_per_launch"):
+    """A per-launch figure of the step kernel from the committed ncu summary, if still current.
 
-    The summary carries "kernel_hash: <h>" and "dram_bytes_per_launch: <n>" lines;
-    the figure is dropped (None) once the kernel sources have changed since.
+    The summary carries "kernel_hash: <h>" and "<name>: <n>" lines (DRAM bytes,
+    warp-instructions); the figure is dropped (None) once the kernel sources
+    have changed since.
     """
     try:
         fields = {}
@@ -117,10 +118,18 @@ def recorded_traffic():
                     k, v = line.split(":", 1)
                     fields[k.strip()] = v.strip()
         if fields.get("kernel_hash") == kernel_hash():
-            return float(fields["dram_bytes_per_launch"])
+            return float(fields[name])
     except Exception:
         pass
     return None
+
+
+def recorded_traffic():
+    return recorded_counter("dram_bytes_per_launch")
+
+
+# Warp-instruction issue peak: 152 SMs x 4 schedulers x 1 instruction per clock x 2.07 GHz
+ISSUE_PEAK_GINST = 152 * 4 * 2.07
 
 
 class ClockSampler:
@@ -450,7 +459,9 @@ def run_gpu(args, world, rank, local):
     avg_launch_s = step_ms / 1e3 / max(step_launches, 1)
     achieved = alg_bytes_per_pos * pos_per_launch / avg_launch_s / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = recorded_traffic()
+    traffic = recorded_traffic()       # ncu DRAM bytes of one launch of 64 positions
+    if traffic is not None:
+        traffic = round(traffic * pos_per_launch / 64)
     kernel_share = {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4) for k, v in prof.items()}
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 5), "peak_source": peak_kind,
@@ -463,6 +474,15 @@ def run_gpu(args, world, rank, local):
     roofline["fp32"] = {"achieved": round(flops / avg_launch_s / 1e12, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
                         "unit": "TFLOP/s", "frac": round(flops / avg_launch_s / 1e12 / FP32_PEAK_TFLOPS, 5),
                         "flops_per_launch": int(flops), "peak_source": "derived: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+    inst = recorded_counter("warp_instructions_per_launch")
+    if inst is not None:
+        # the ncu count is for a launch of 64 positions; scale to this run's average launch
+        inst_avg = inst * pos_per_launch / 64
+        roofline["issue"] = {"achieved": round(inst_avg / avg_launch_s / 1e9, 2), "peak": round(ISSUE_PEAK_GINST, 2),
+                             "unit": "G warp-instructions/s",
+                             "frac": round(inst_avg / avg_launch_s / 1e9 / ISSUE_PEAK_GINST, 5),
+                             "instructions_per_launch": int(inst_avg),
+                             "peak_source": "derived: 152 SMs x 4 schedulers x 2.07 GHz; count from the ncu summary"}
 
     if rank != 0:
         return
