@@ -926,6 +926,8 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
       static_assert(hc * wc % NT == 0, "coarse slab must split evenly");
       const float* Wz = a.lv.Wz[0];
       const float2* WR = a.lv.WR[0];
+      float2* __restrict__ const Z1w = Zl[1];
+      float2* __restrict__ const R1w = Rl[1];
 #pragma unroll
       for (int t = 0; t < PC; ++t) {
         const int p = tid + t * NT;
@@ -940,8 +942,8 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
             zs = cadd(zs, cscale(zk, Wz[r * M + c]));
             rs = cadd(rs, cmul(WR[r * M + c], rowbuf[lr * SR + c]));
           }
-        Zl[1][i * sc + j] = cscale(zs, 0.25f);
-        Rl[1][i * sc + j] = cscale(rs, 0.25f);
+        Z1w[i * sc + j] = cscale(zs, 0.25f);
+        R1w[i * sc + j] = cscale(rs, 0.25f);
       }
     }
     __syncthreads();
@@ -949,6 +951,10 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
       const int wf = M >> l, sf = wf + 1, hf = wf / C, wc = wf >> 1, hc = wc / C, sc = wc + 1;
       const float* Wz = a.lv.Wz[l];
       const float2* WR = a.lv.WR[l];
+      const float2* __restrict__ const Zf = Zl[l];
+      const float2* __restrict__ const Rf = Rl[l];
+      float2* __restrict__ const Zc = Zl[l + 1];
+      float2* __restrict__ const Rc = Rl[l + 1];
       for (int p = tid; p < hc * wc; p += NT) {
         const int i = p / wc, j = p % wc;
         float2 zs = czero(), rs = czero();
@@ -957,11 +963,11 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
 #pragma unroll
           for (int dx = 0; dx < 2; ++dx) {
             const int lr = 2 * i + dy, r = rank * hf + lr, c = 2 * j + dx;
-            zs = cadd(zs, cscale(Zl[l][lr * sf + c], Wz[r * wf + c]));
-            rs = cadd(rs, cmul(WR[r * wf + c], Rl[l][lr * sf + c]));
+            zs = cadd(zs, cscale(Zf[lr * sf + c], Wz[r * wf + c]));
+            rs = cadd(rs, cmul(WR[r * wf + c], Rf[lr * sf + c]));
           }
-        Zl[l + 1][i * sc + j] = cscale(zs, 0.25f);
-        Rl[l + 1][i * sc + j] = cscale(rs, 0.25f);
+        Zc[i * sc + j] = cscale(zs, 0.25f);
+        Rc[i * sc + j] = cscale(rs, 0.25f);
       }
       __syncthreads();
     }
@@ -970,10 +976,12 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
       const int wl = M >> l, hl = wl / C, sl = wl + 1;
       const float2* G = a.lv.G[l];
       const float2* Q = a.lv.Q[l];
+      float2* __restrict__ const Zw = Zl[l];
+      const float2* __restrict__ const Rw = Rl[l];
       for (int p = tid; p < hl * wl; p += NT) {
         const int i = p / wl, j = p % wl, gi = rank * hl + i;
-        const float2 z = Zl[l][i * sl + j];
-        Zl[l][i * sl + j] = cmul(G[gi * wl + j], csub(Rl[l][i * sl + j], cmul(Q[gi * wl + j], z)));
+        const float2 z = Zw[i * sl + j];
+        Zw[i * sl + j] = cmul(G[gi * wl + j], csub(Rw[i * sl + j], cmul(Q[gi * wl + j], z)));
       }
     }
     // back up: c_l = I_H^h c_{l+1} + G_l (R_l - Q_l (z_l + I_H^h c_{l+1}))
@@ -986,12 +994,15 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
       const int wl = M >> l, hl = wl / C, sl = wl + 1, wc = wl >> 1, sc = wc + 1;
       const float2* G = a.lv.G[l];
       const float2* Q = a.lv.Q[l];
+      float2* __restrict__ const Zw = Zl[l];
+      const float2* __restrict__ const Rw = Rl[l];
+      const float2* __restrict__ const Zc = Zl[l + 1];
 #pragma unroll 4
       for (int p = tid; p < hl * wl; p += NT) {
         const int i = p / wl, j = p % wl, gi = rank * hl + i;
-        const float2 pro = prolong_halo<float2>(Zl[l + 1], sc, wc, i, j, a.prolong);
-        const float2 zp = cadd(Zl[l][i * sl + j], pro);
-        Zl[l][i * sl + j] = cadd(pro, cmul(G[gi * wl + j], csub(Rl[l][i * sl + j], cmul(Q[gi * wl + j], zp))));
+        const float2 pro = prolong_halo<float2>(Zc, sc, wc, i, j, a.prolong);
+        const float2 zp = cadd(Zw[i * sl + j], pro);
+        Zw[i * sl + j] = cadd(pro, cmul(G[gi * wl + j], csub(Rw[i * sl + j], cmul(Q[gi * wl + j], zp))));
       }
     }
     if (halo) {
