@@ -315,6 +315,15 @@ emg_status emg_dft2_bf16x3(const float* in, float* out, int32_t m, int32_t count
                            emg_stream_t stream);
 
 /*
+ * Check of the failure path of the tensor-core kernel's waits: one CTA waits,
+ * with the same bounded mbarrier wait, on a barrier that nothing arrives on.
+ * The wait gives up after its limit (1 s) and records that in a device flag,
+ * as a stalled pipeline would; *gave_up receives the flag (1 expected).  The
+ * device stays usable.  Synchronises the device.  EMG_EINVAL for NULL.
+ */
+emg_status emg_selftest_bounded_wait(int32_t* gave_up);
+
+/*
  * FFT tiling: the number of CTAs that share one scan position in the step
  * kernel (1 or 2 for m <= 32; 2 or 4 for m = 64; 2, 4 or 8 for m = 128; 8 for
  * m = 256).  It changes speed only: results are identical for every valid

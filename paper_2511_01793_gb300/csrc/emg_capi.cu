@@ -1119,6 +1119,24 @@ emg_status emg_fft2(const float* in, float* out, int32_t m, int32_t count, int32
   return e == cudaSuccess ? EMG_OK : EMG_ECUDA;
 }
 
+emg_status emg_selftest_bounded_wait(int32_t* gave_up) {
+  if (!gave_up) return EMG_EINVAL;
+  *gave_up = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || ensure_device_init(dev) != cudaSuccess) return EMG_ECUDA;
+  int* flag = nullptr;
+  if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return EMG_ENOMEM;
+  int h = 0;
+  cudaError_t e = cudaMemset(flag, 0, sizeof(int));
+  if (e == cudaSuccess) e = emg::launch_wait_selftest(flag, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, flag, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(flag);
+  if (e != cudaSuccess) return EMG_ECUDA;
+  *gave_up = h;
+  return EMG_OK;
+}
+
 emg_status emg_dft2_bf16x3(const float* in, float* out, int32_t m, int32_t count, int32_t inverse,
                            emg_stream_t stream) {
   if (!in || !out || in == out || count < 0 || (inverse != 0 && inverse != 1)) return EMG_EINVAL;

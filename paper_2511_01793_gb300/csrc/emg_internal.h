@@ -186,6 +186,8 @@ cudaError_t tc_dft2(TcWork* w, const float2* in, float2* out, int count, int inv
 // a1-a4 of a minibatch: psi_k, Psi_k, modulus replacement, R_k.
 cudaError_t tc_exit_waves(TcWork* w, const TcStepArgs& a, cudaStream_t s);
 cudaError_t launch_tc_amp(const float* d, float* amp_t, int m, int n_pos, cudaStream_t s);
+// One bounded mbarrier wait that nothing satisfies; sets *err when it gives up.
+cudaError_t launch_wait_selftest(int* err, cudaStream_t s);
 int step_smem_limit();
 
 }  // namespace emg

@@ -505,6 +505,21 @@ __global__ void __launch_bounds__(256) k_tc_amp(const float* __restrict__ d, flo
   }
 }
 
+// Exercises the give-up path of the bounded wait: one thread waits on an
+// mbarrier that nothing arrives on, exactly as the roles of k_tc_dft wait, and
+// records the expiry in *err.  No copy or MMA is in flight, so nothing else
+// needs draining.
+__global__ void k_wait_selftest(int* err) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, &abort_flag)) *err = 1;
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 
@@ -787,6 +802,11 @@ cudaError_t tc_exit_waves(TcWork* w, const TcStepArgs& t, cudaStream_t s) {
   a.out_hi = a.out_lo = nullptr;
   a.out_f32 = t.R;
   return launch_pass<kEpiF32>(w->amap[1][0], w->amap[1][1], G[0], G[1], rows, w->sms, a, s);
+}
+
+cudaError_t launch_wait_selftest(int* err, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(err);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_tc_amp(const float* d, float* amp_t, int m, int n_pos, cudaStream_t s) {

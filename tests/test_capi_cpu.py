@@ -109,6 +109,10 @@ def test_context_free_calls_validate_arguments(lib):
     assert lib.emg_dft2_bf16x3(0x10, 0x20, 64, 1, 0, None) == emg.EMG_ENOTSUP
     assert lib.emg_dft2_bf16x3(0x10, 0x20, 256, 0, 0, None) == emg.EMG_OK      # empty batch
     assert lib.emg_set_gradient_chunk(None, 0) == emg.EMG_EINVAL
+    assert lib.emg_selftest_bounded_wait(None) == emg.EMG_EINVAL
+    assert lib.emg_set_minibatch(None, 4) == emg.EMG_EINVAL
+    assert lib.emg_set_scatter(None, 0) == emg.EMG_EINVAL
+    assert lib.emg_autotune_search(None, None, None) == emg.EMG_EINVAL
     assert lib.emg_set_cluster(None, 2) == emg.EMG_EINVAL
     lib.emg_destroy(None)  # no-op
 

@@ -204,3 +204,24 @@ def test_full_size_precision_minibatch_matches_the_oracle(lib, torch):
         print(f"dft={dft}: object {e_z:.2e} probe {e_q:.2e}")
         assert e_z <= tol and e_q <= tol
         assert np.array_equal(z_g[~mask], z0.astype(np.complex128)[~mask])
+
+
+def test_bounded_wait_gives_up_reports_and_leaves_the_device_usable(lib, torch):
+    """A wait on an mbarrier that nothing arrives on (the tensor-core kernel's wait)
+    gives up after its 1 s limit and sets the device flag; the GPU then still
+    computes a correct tensor-core transform."""
+    import time
+
+    t0 = time.perf_counter()
+    gave_up = lib.emg_selftest_bounded_wait()
+    dt = time.perf_counter() - t0
+    assert gave_up == 1
+    assert 0.9 <= dt < 60.0
+    rng = np.random.default_rng(11)
+    x = (rng.standard_normal((2, 128, 128)) + 1j * rng.standard_normal((2, 128, 128))).astype(np.complex64)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    lib.emg_dft2_bf16x3(xd.data_ptr(), yd.data_ptr(), 128, 2, False)
+    torch.cuda.synchronize()
+    want = np.stack([O.dft2(t.astype(np.complex128)) for t in x])
+    assert rel_err(yd.cpu().numpy().astype(np.complex128), want) <= TOL
