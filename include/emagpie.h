@@ -324,6 +324,13 @@ emg_status emg_dft2_bf16x3(const float* in, float* out, int32_t m, int32_t count
 emg_status emg_selftest_bounded_wait(int32_t* gave_up);
 
 /*
+ * Host-side fault injection for tests: the library's next device allocation
+ * after `after` successful ones fails once (as if the device were out of
+ * memory); -1 disables.  Process-wide.  EMG_EINVAL for after < -1.
+ */
+emg_status emg_debug_fail_alloc(int32_t after);
+
+/*
  * FFT tiling: the number of CTAs that share one scan position in the step
  * kernel (1 or 2 for m <= 32; 2 or 4 for m = 64; 2, 4 or 8 for m = 128; 8 for
  * m = 256).  It changes speed only: results are identical for every valid

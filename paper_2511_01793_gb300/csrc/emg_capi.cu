@@ -6,10 +6,13 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/emagpie.h"
 #include "emg_internal.h"
@@ -159,11 +162,22 @@ emg_status cuda_fail(emg_ctx* c, cudaError_t e, const char* where) {
   } while (0)
 
 // Brackets one launch with a pair of events on the context's stream when profiling.
+// NVTX range for the lifetime of a scope (a no-op unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+const char* const kKindNames[kKinds] = {"emg:prep", "emg:step", "emg:apply", "emg:other", "emg:dft"};
+
 struct LaunchMark {
   emg_ctx* c;
   int kind;
   cudaEvent_t stop = nullptr;
-  LaunchMark(emg_ctx* ctx, int k, int n = 1) : c(ctx), kind(k) {
+  NvtxRange range;
+  LaunchMark(emg_ctx* ctx, int k, int n = 1) : c(ctx), kind(k), range(kKindNames[k]) {
     c->launches[k] += n;
     if (!c->profile) return;
     if (c->ev_used + 2 > c->ev_pool.size()) {
@@ -219,10 +233,18 @@ emg_status validate_params(emg_ctx* c, const emg_params* p, int m, int n_pos) {
   return EMG_OK;
 }
 
+// Host-side fault injection (emg_debug_fail_alloc): the library's device
+// allocation after this many successful ones fails once; -1 disables.
+std::atomic<int> g_fail_alloc_after{-1};
+
 template <typename T>
 cudaError_t dmalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) return cudaSuccess;
+  int n = g_fail_alloc_after.load();
+  while (n >= 0 && !g_fail_alloc_after.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n == 0) return cudaErrorMemoryAllocation;
   return cudaMalloc((void**)p, count * sizeof(T));
 }
 
@@ -844,6 +866,7 @@ const char* emg_status_string(emg_status s) {
 }
 
 emg_status emg_create(emg_ctx** out, const emg_problem* pr, const emg_params* par, emg_stream_t stream) {
+  NvtxRange nvtx_range("emg_create");
   if (!out) return EMG_EINVAL;
   *out = nullptr;
   if (!pr || !par) return EMG_EINVAL;
@@ -944,6 +967,7 @@ emg_status emg_normalize_probe(emg_ctx* c) {
 }
 
 emg_status emg_step_minibatch(emg_ctx* c, const int32_t* idx, int32_t b, double* sampled_misfit) {
+  NvtxRange nvtx_range("emg_step_minibatch");
   if (!c) return EMG_EINVAL;
   emg_status st = check_bound(c);
   if (st != EMG_OK) return st;
@@ -994,6 +1018,7 @@ emg_status emg_set_verify(emg_ctx* c, int32_t verify) {
 
 emg_status emg_run_epochs(emg_ctx* c, int32_t n_epochs, const int32_t* order, double* running_misfit,
                           double* misfit) {
+  NvtxRange nvtx_range("emg_run_epochs");
   if (!c) return EMG_EINVAL;
   emg_status st = check_bound(c);
   if (st != EMG_OK) return st;
@@ -1064,6 +1089,7 @@ emg_status emg_schedule_permutation(uint64_t seed, int64_t epoch, int32_t n, int
 emg_status emg_reconstruct_host(emg_ctx* c, const float* intensity, float* object, float* probe,
                                 int32_t n_epochs, const int32_t* order, double* running_misfit,
                                 double* misfit) {
+  NvtxRange nvtx_range("emg_reconstruct_host");
   if (!c) return EMG_EINVAL;
   if (!intensity || !object || !probe) return fail(c, EMG_EINVAL, "NULL host buffer");
   DeviceGuard g(c->device);
@@ -1119,6 +1145,12 @@ emg_status emg_fft2(const float* in, float* out, int32_t m, int32_t count, int32
   return e == cudaSuccess ? EMG_OK : EMG_ECUDA;
 }
 
+emg_status emg_debug_fail_alloc(int32_t after) {
+  if (after < -1) return EMG_EINVAL;
+  g_fail_alloc_after.store(after);
+  return EMG_OK;
+}
+
 emg_status emg_selftest_bounded_wait(int32_t* gave_up) {
   if (!gave_up) return EMG_EINVAL;
   *gave_up = 0;
@@ -1158,6 +1190,7 @@ emg_status emg_dft2_bf16x3(const float* in, float* out, int32_t m, int32_t count
 
 emg_status emg_misfit_gradient(emg_ctx* c, const float* object, const float* probe, float* grad_object,
                                float* grad_probe, double* misfit) {
+  NvtxRange nvtx_range("emg_misfit_gradient");
   if (!c) return EMG_EINVAL;
   if (!object || !probe) return fail(c, EMG_EINVAL, "object or probe is NULL");
   DeviceGuard g(c->device);
@@ -1262,6 +1295,7 @@ emg_status emg_set_scatter(emg_ctx* c, int32_t scatter) {
 }
 
 emg_status emg_autotune_search(emg_ctx* c, const emg_tune_request* req, emg_tune_result* res) {
+  NvtxRange nvtx_range("emg_autotune_search");
   if (!c) return EMG_EINVAL;
   if (!req || !res) return fail(c, EMG_EINVAL, "request or result is NULL");
   if (req->n_minibatch < 0 || (req->n_minibatch > 0 && !req->minibatch) || req->trial_epochs < 1)
@@ -1288,6 +1322,7 @@ emg_status emg_autotune_search(emg_ctx* c, const emg_tune_request* req, emg_tune
   float2* keep_p = c->probe;
   const int64_t keep_epoch = c->epoch;
   const int keep_profile = c->profile;
+  const int keep_b = c->par.minibatch, keep_cl = c->cluster, keep_sc = c->par.scatter;
   int64_t keep_launches[kKinds];
   for (int i = 0; i < kKinds; ++i) keep_launches[i] = c->launches[i];
   c->profile = 0;
@@ -1347,6 +1382,11 @@ emg_status emg_autotune_search(emg_ctx* c, const emg_tune_request* req, emg_tune
   c->probe = keep_p;
   c->epoch = keep_epoch;
   c->profile = keep_profile;
+  if (st != EMG_OK) {  // leave the settings as they were (best effort; the error is reported)
+    c->cluster = keep_cl;
+    set_minibatch_impl(c, keep_b);
+    set_scatter_impl(c, keep_sc);
+  }
   for (int i = 0; i < kKinds; ++i) c->launches[i] = keep_launches[i];
   drop_graphs(c);  // captured with the private buffers
   cudaEventDestroy(e0);
@@ -1363,6 +1403,7 @@ emg_status emg_autotune_search(emg_ctx* c, const emg_tune_request* req, emg_tune
 }
 
 emg_status emg_autotune(emg_ctx* c, int32_t* chosen, double* ms_per_minibatch) {
+  NvtxRange nvtx_range("emg_autotune");
   if (!c) return EMG_EINVAL;
   emg_status st = check_bound(c);
   if (st != EMG_OK) return st;
@@ -1461,6 +1502,7 @@ emg_status emg_batch_create(emg_batch** out, emg_ctx* const* ctxs, int32_t count
 }
 
 emg_status emg_batch_run_epochs(emg_batch* b, int32_t n_epochs, emg_stream_t stream) {
+  NvtxRange nvtx_range("emg_batch_run_epochs");
   if (!b || n_epochs < 0) return EMG_EINVAL;
   if (n_epochs == 0) return EMG_OK;
   DeviceGuard g(b->device);

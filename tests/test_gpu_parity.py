@@ -495,3 +495,34 @@ def test_pinned_host_intensity_equals_device_intensity(lib, torch, m, levels):
         c2.close()
         c3.close()
     c1.close()
+
+
+@pytest.mark.parametrize("scatter,dft", [(0, 0), (1, 1)])
+def test_create_releases_everything_when_an_allocation_fails(lib, torch, scatter, dft):
+    """Host-side fault injection: each device allocation of emg_create fails in
+    turn; every attempt returns EMG_ENOMEM and leaves no device memory behind."""
+    m = 128
+    case = Case(n=2 * m + 40, m=m, side=3, seed=78)
+    p = oracle_params(minibatch=4, levels=2)
+    make_context(lib, case, p, scatter=scatter, dft=dft).close()   # lazy CUDA state in place
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free0 = torch.cuda.mem_get_info()[0]
+    failures = 0
+    try:
+        for after in range(64):
+            lib.emg_debug_fail_alloc(after)
+            try:
+                ctx = make_context(lib, case, p, scatter=scatter, dft=dft)
+            except lib.EmgError as e:
+                assert e.status == lib.EMG_ENOMEM
+                failures += 1
+                continue
+            ctx.close()      # `after` exceeded the allocations of one create
+            break
+    finally:
+        lib.emg_debug_fail_alloc(-1)
+    assert failures >= 10
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) <= 4 << 20
