@@ -331,6 +331,24 @@ emg_status emg_selftest_bounded_wait(int32_t* gave_up);
 emg_status emg_debug_fail_alloc(int32_t after);
 
 /*
+ * Bounds-check build only (compiled with -DEMG_BOUNDS_CHECK): *mask receives
+ * the error word and the word is cleared.  Bit i set: an index check at site
+ * i failed and its access was skipped (sites: 0 order entry and 1 minibatch
+ * slot in the step kernels, 2 multigrid level index, 3 order entry, 4 patch
+ * slot and 5 object index in the combine).  Synchronous.  EMG_ENOTSUP (with
+ * *mask = 0) in a build without the checks.
+ */
+emg_status emg_debug_bounds_errors(uint32_t* mask);
+
+/*
+ * Bounds-check build only: runs one check that must fail (an index equal to
+ * its bound, site 2), whose store is skipped, and returns the error word in
+ * *mask (bit 2 expected), clearing it.  Synchronises the device.  EMG_ENOTSUP
+ * in a build without the checks.
+ */
+emg_status emg_debug_bounds_selftest(uint32_t* mask);
+
+/*
  * FFT tiling: the number of CTAs that share one scan position in the step
  * kernel (1 or 2 for m <= 32; 2 or 4 for m = 64; 2, 4 or 8 for m = 128; 8 for
  * m = 256).  It changes speed only: results are identical for every valid

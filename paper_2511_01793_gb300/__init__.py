@@ -28,7 +28,8 @@ __all__ = [
     "emg_set_epoch", "emg_schedule_permutation", "emg_stopping_epoch", "emg_run_until", "emg_reconstruct_host",
     "emg_simulate_intensity", "emg_fft2", "emg_dft2_bf16x3", "emg_step_minibatch_noalloc", "emg_misfit_gradient",
     "emg_set_cluster", "emg_set_gradient_chunk", "emg_autotune", "emg_set_minibatch", "emg_set_scatter",
-    "emg_selftest_bounded_wait", "emg_debug_fail_alloc",
+    "emg_selftest_bounded_wait", "emg_debug_fail_alloc", "emg_debug_bounds_errors",
+    "emg_debug_bounds_selftest",
     "emg_autotune_search", "EmgTuneRequest", "EmgTuneResult", "emg_batch_create", "emg_batch_run_epochs", "emg_batch_destroy",
     "emg_set_profiling",
     "emg_profile_read",
@@ -112,6 +113,8 @@ _SIGS = {
     "emg_set_minibatch": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "emg_selftest_bounded_wait": (ctypes.c_int, [_I32P]),
     "emg_debug_fail_alloc": (ctypes.c_int, [ctypes.c_int32]),
+    "emg_debug_bounds_errors": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
+    "emg_debug_bounds_selftest": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
     "emg_set_scatter": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "emg_autotune_search": (ctypes.c_int, [_VP, ctypes.POINTER(EmgTuneRequest), ctypes.POINTER(EmgTuneResult)]),
     "emg_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int32]),
@@ -346,6 +349,26 @@ def emg_set_cluster(ctx: int, cluster: int) -> None:
 def emg_debug_fail_alloc(after: int) -> None:
     """Fault injection: the device allocation after `after` successful ones fails once (-1: off)."""
     _check(load().emg_debug_fail_alloc(after), "emg_debug_fail_alloc")
+
+
+def emg_debug_bounds_errors() -> Optional[int]:
+    """The bounds-check build's error word (cleared on read); None in a build without the checks."""
+    out = ctypes.c_uint32()
+    st = load().emg_debug_bounds_errors(ctypes.byref(out))
+    if st == EMG_ENOTSUP:
+        return None
+    _check(st, "emg_debug_bounds_errors")
+    return out.value
+
+
+def emg_debug_bounds_selftest() -> Optional[int]:
+    """The error word after one check that must fail; None in a build without the checks."""
+    out = ctypes.c_uint32()
+    st = load().emg_debug_bounds_selftest(ctypes.byref(out))
+    if st == EMG_ENOTSUP:
+        return None
+    _check(st, "emg_debug_bounds_selftest")
+    return out.value
 
 
 def emg_selftest_bounded_wait() -> int:

@@ -24,8 +24,26 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-ftz=true", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
 
 
+# Build variants, selected by the environment variable EMG_BUILD_VARIANT; each
+# builds into its own directory under _lib/.  "boundscheck" adds the index
+# checks of the kernels (emg_debug_bounds_errors reads what they record).
+VARIANTS = {"": [], "boundscheck": ["-DEMG_BOUNDS_CHECK"]}
+
+
+def variant() -> str:
+    v = os.environ.get("EMG_BUILD_VARIANT", "")
+    if v not in VARIANTS:
+        raise RuntimeError(f"unknown EMG_BUILD_VARIANT {v!r}; known: {sorted(VARIANTS)}")
+    return v
+
+
+def out_dir() -> str:
+    v = variant()
+    return os.path.join(OUT_DIR, v) if v else OUT_DIR
+
+
 def lib_path() -> str:
-    return os.path.join(OUT_DIR, LIB_NAME)
+    return os.path.join(out_dir(), LIB_NAME)
 
 
 def _nvcc() -> str:
@@ -54,9 +72,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     EMG_NVCC_EXTRA (whitespace-separated, e.g. tuning macros such as
     -DEMG_UPDATE_GROUP=8); both are part of the build stamp.
     """
-    extra_flags = list(extra_flags) + os.environ.get("EMG_NVCC_EXTRA", "").split()
-    os.makedirs(OUT_DIR, exist_ok=True)
-    stamp = os.path.join(OUT_DIR, "build.sha256")
+    extra_flags = list(extra_flags) + os.environ.get("EMG_NVCC_EXTRA", "").split() + VARIANTS[variant()]
+    odir = out_dir()
+    os.makedirs(odir, exist_ok=True)
+    stamp = os.path.join(odir, "build.sha256")
     digest = _digest(extra_flags)
     if not force and os.path.exists(lib_path()) and os.path.exists(stamp):
         with open(stamp) as f:
@@ -66,7 +85,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     procs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(odir, src.replace(".cu", ".o"))
         objs.append(obj)
         cmd = [nvcc, *ARCH, *CFLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:

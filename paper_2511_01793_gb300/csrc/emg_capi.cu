@@ -421,6 +421,8 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   sa.order = d_idx;
   sa.mq = pa.mq_read;
   sa.n_rows = c->n_rows;
+  sa.n_pos = c->n_pos;
+  sa.b = b;
   sa.n_cols = c->n_cols;
   sa.levels = c->par.levels;
   sa.prolong = c->par.prolong;
@@ -474,6 +476,7 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   aa.pos = c->d_pos;
   aa.order = d_idx;
   aa.b = b;
+  aa.n_pos = c->n_pos;
   aa.n_rows = c->n_rows;
   aa.n_cols = c->n_cols;
   aa.m = c->m;
@@ -1142,6 +1145,28 @@ emg_status emg_fft2(const float* in, float* out, int32_t m, int32_t count, int32
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || ensure_device_init(dev) != cudaSuccess) return EMG_ECUDA;
   cudaError_t e = emg::launch_fft2(m, (const float2*)in, (float2*)out, count, inverse, (cudaStream_t)stream);
+  return e == cudaSuccess ? EMG_OK : EMG_ECUDA;
+}
+
+emg_status emg_debug_bounds_errors(uint32_t* mask) {
+  if (!mask) return EMG_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || ensure_device_init(dev) != cudaSuccess) return EMG_ECUDA;
+  unsigned m = 0;
+  const cudaError_t e = emg::bounds_errors_take(&m);
+  *mask = m;
+  if (e == cudaErrorNotSupported) return EMG_ENOTSUP;
+  return e == cudaSuccess ? EMG_OK : EMG_ECUDA;
+}
+
+emg_status emg_debug_bounds_selftest(uint32_t* mask) {
+  if (!mask) return EMG_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || ensure_device_init(dev) != cudaSuccess) return EMG_ECUDA;
+  unsigned m = 0;
+  const cudaError_t e = emg::bounds_probe(&m);
+  *mask = m;
+  if (e == cudaErrorNotSupported) return EMG_ENOTSUP;
   return e == cudaSuccess ? EMG_OK : EMG_ECUDA;
 }
 

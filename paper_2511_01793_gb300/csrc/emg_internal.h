@@ -9,6 +9,22 @@ namespace emg {
 
 constexpr int kMaxLevels = 7;
 
+// Index-check sites of the bounds-check build (-DEMG_BOUNDS_CHECK): bit i of
+// the device error word (emg_debug_bounds_errors) records a failed check at
+// site i; the access is then skipped (a load reads 0 or index 0 instead).
+enum BoundsSite : int {
+  kBcOrder = 0,        // step kernels: order entry outside 0..n_pos-1
+  kBcPatchWrite = 1,   // step kernels: minibatch slot outside 0..b-1
+  kBcLevel = 2,        // step kernel: multigrid level array index
+  kBcApplyOrder = 3,   // combine: order entry outside 0..n_pos-1
+  kBcApplyPatch = 4,   // combine: patch slot outside 0..b-1
+  kBcApplyObject = 5,  // combine: object index
+};
+// Reads and clears the error word (cudaErrorNotSupported without the checks).
+cudaError_t bounds_errors_take(unsigned* out);
+// One failing check (site kBcLevel) whose access is skipped; then bounds_errors_take.
+cudaError_t bounds_probe(unsigned* out);
+
 // Probe-only multigrid arrays of one minibatch (Sec. 3.2, Eq. def_weights and
 // Eq. downsampled_terms).  Level l has side m >> l.
 //   G[l]  = conj(Q_l) / (u_l + |Q_l|^2)               (closed-form gain, 0/0 := 0)
@@ -48,6 +64,7 @@ struct StepArgs {
   const int32_t* order;         // positions of this minibatch, [b]
   const unsigned* mq;           // max|Q|^2 of the probe (float bits), read by the cluster step
   int n_rows, n_cols;
+  int n_pos, b;                 // positions of the problem and of this minibatch (index checks)
   int levels, prolong, joint, verify;
   int cluster;                  // CTAs per position: 1 (m <= 32 only), 2, 4 or 8 (m = 256)
   float alpha;                  // rPIE constant (level-0 gain formed in the cluster step)
@@ -75,6 +92,7 @@ struct ApplyArgs {
   const int32_t* pos;
   const int32_t* order;
   int b, n_rows, n_cols, m, combine;
+  int n_pos;                    // positions of the problem (index checks)
   const float2* zt;
   const float2* qt;
   const float* mu;

@@ -17,6 +17,62 @@
 #include "emg_internal.h"
 
 namespace emg {
+namespace {
+#ifdef EMG_BOUNDS_CHECK
+__device__ unsigned g_bounds_error;
+__device__ __forceinline__ bool in_bounds(long long i, long long n, int site) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(&g_bounds_error, 1u << site);
+  return false;
+}
+#define EMG_INB(i, n, site) in_bounds((long long)(i), (long long)(n), (site))
+#else
+#define EMG_INB(i, n, site) true
+#endif
+}  // namespace
+
+#ifdef EMG_BOUNDS_CHECK
+namespace {
+// Exercises the recording path of the checks: index n against a bound of n
+// fails the check, so the store is skipped (buf holds n + 1 floats regardless).
+__global__ void k_bounds_probe(float* buf, int n) {
+  if (threadIdx.x == 0 && EMG_INB(n, n, kBcLevel)) buf[n] = 1.f;
+}
+}  // namespace
+#endif
+
+cudaError_t bounds_probe(unsigned* out) {
+#ifdef EMG_BOUNDS_CHECK
+  float* buf = nullptr;
+  const int n = 32;
+  cudaError_t e = cudaMalloc(&buf, (n + 1) * sizeof(float));
+  if (e != cudaSuccess) return e;
+  k_bounds_probe<<<1, 32>>>(buf, n);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(buf);
+  if (e != cudaSuccess) return e;
+  return bounds_errors_take(out);
+#else
+  *out = 0;
+  return cudaErrorNotSupported;
+#endif
+}
+
+cudaError_t bounds_errors_take(unsigned* out) {
+#ifdef EMG_BOUNDS_CHECK
+  unsigned zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_bounds_error, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_bounds_error, &zero, sizeof(unsigned));
+  return e;
+#else
+  *out = 0;
+  return cudaErrorNotSupported;
+#endif
+}
+}  // namespace emg
+
+namespace emg {
 
 namespace {
 
@@ -504,7 +560,9 @@ __global__ void __launch_bounds__(StepThreads<M>::value) k_step(const StepArgs a
   __shared__ float redf[NT / 32];
   const int tid = threadIdx.x;
   const int kb = blockIdx.x;
-  const int k = a.order[kb];
+  int k = a.order[kb];
+  if (!EMG_INB(k, a.n_pos, kBcOrder)) k = 0;
+  const bool slot_ok = EMG_INB(kb, a.b, kBcPatchWrite);
   const int o_r = a.pos[2 * k], o_c = a.pos[2 * k + 1];
   float2* buf = sm;
 
@@ -673,9 +731,9 @@ __global__ void __launch_bounds__(StepThreads<M>::value) k_step(const StepArgs a
     if (a.s_num)
       scatter_atomic(a.s_num, a.s_den, a.combine, a.n_rows, a.n_cols, o_r + r, o_c + c, zn, zk,
                      fmaf(a.w_eps, MQ, cabs2(q)));
-    else
+    else if (slot_ok)
       zt[p] = zn;
-    qt[p] = qn;
+    if (slot_ok) qt[p] = qn;
     if (a.verify) acc_after += cabs2(csub(cmul(qn, zn), R));
   }
   double phi_after = 0.0;
@@ -796,7 +854,9 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
   __shared__ float redf[NT / 32];
   const int tid = threadIdx.x;
   const int kb = blockIdx.x / C;
-  const int k = a.order[kb];
+  int k = a.order[kb];
+  if (!EMG_INB(k, a.n_pos, kBcOrder)) k = 0;
+  const bool slot_ok = EMG_INB(kb, a.b, kBcPatchWrite);
   const int o_r = a.pos[2 * k], o_c = a.pos[2 * k + 1];
   const int row0 = rank * H;
 
@@ -963,8 +1023,9 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
 #pragma unroll
           for (int dx = 0; dx < 2; ++dx) {
             const int lr = 2 * i + dy, r = rank * hf + lr, c = 2 * j + dx;
-            zs = cadd(zs, cscale(Zf[lr * sf + c], Wz[r * wf + c]));
-            rs = cadd(rs, cmul(WR[r * wf + c], Rf[lr * sf + c]));
+            const int wi = EMG_INB(r * wf + c, wf * wf, kBcLevel) ? r * wf + c : 0;
+            zs = cadd(zs, cscale(Zf[lr * sf + c], Wz[wi]));
+            rs = cadd(rs, cmul(WR[wi], Rf[lr * sf + c]));
           }
         Zc[i * sc + j] = cscale(zs, 0.25f);
         Rc[i * sc + j] = cscale(rs, 0.25f);
@@ -980,8 +1041,9 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
       const float2* __restrict__ const Rw = Rl[l];
       for (int p = tid; p < hl * wl; p += NT) {
         const int i = p / wl, j = p % wl, gi = rank * hl + i;
+        const int li = EMG_INB(gi * wl + j, wl * wl, kBcLevel) ? gi * wl + j : 0;
         const float2 z = Zw[i * sl + j];
-        Zw[i * sl + j] = cmul(G[gi * wl + j], csub(Rw[i * sl + j], cmul(Q[gi * wl + j], z)));
+        Zw[i * sl + j] = cmul(G[li], csub(Rw[i * sl + j], cmul(Q[li], z)));
       }
     }
     // back up: c_l = I_H^h c_{l+1} + G_l (R_l - Q_l (z_l + I_H^h c_{l+1}))
@@ -1000,9 +1062,10 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
 #pragma unroll 4
       for (int p = tid; p < hl * wl; p += NT) {
         const int i = p / wl, j = p % wl, gi = rank * hl + i;
+        const int li = EMG_INB(gi * wl + j, wl * wl, kBcLevel) ? gi * wl + j : 0;
         const float2 pro = prolong_halo<float2>(Zc, sc, wc, i, j, a.prolong);
         const float2 zp = cadd(Zw[i * sl + j], pro);
-        Zw[i * sl + j] = cadd(pro, cmul(G[gi * wl + j], csub(Rw[i * sl + j], cmul(Q[gi * wl + j], zp))));
+        Zw[i * sl + j] = cadd(pro, cmul(G[li], csub(Rw[i * sl + j], cmul(Q[li], zp))));
       }
     }
     if (halo) {
@@ -1058,9 +1121,9 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
     }
     if (a.s_num)
       scatter_atomic(a.s_num, a.s_den, a.combine, a.n_rows, a.n_cols, o_r + r, o_c + c, zn, zk, fmaf(a.w_eps, MQ, a2));
-    else
+    else if (slot_ok)
       zt[r * M + c] = zn;
-    qt[r * M + c] = qn;
+    if (slot_ok) qt[r * M + c] = qn;
     if (a.verify) acc_after += cabs2(csub(cmul(qn, zn), R));
   }
   }
@@ -1414,7 +1477,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
       int pr = 0, pc = 0;
       bool hit = false;
       if (kb < a.b) {
-        const int k = a.order[kb];
+        int k = a.order[kb];
+        if (!EMG_INB(k, a.n_pos, kBcApplyOrder)) k = 0;
         pr = a.pos[2 * k];
         pc = a.pos[2 * k + 1];
         hit = pr < r0 + kApplyTile && pr + m > r0 && pc < c0 + kApplyTile && pc + m > c0;
@@ -1457,7 +1521,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
         in[u] = false;
         if (t < cnt) {
           const int lr = row - list[3 * t + 1], lc = col - list[3 * t + 2];
-          in[u] = (unsigned)lr < (unsigned)m && (unsigned)lc < (unsigned)m;
+          in[u] = (unsigned)lr < (unsigned)m && (unsigned)lc < (unsigned)m &&
+                  EMG_INB(list[3 * t], a.b, kBcApplyPatch);
           if (in[u]) {
             v[u] = a.zt[(size_t)list[3 * t] * mm + lr * m + lc];
             w[u] = a.combine == 0 ? a.wq[lr * m + lc] : 1.f;
@@ -1479,6 +1544,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
     }
     if (!covered) return;
     const size_t gi = (size_t)row * a.n_cols + col;
+    if (!EMG_INB(gi, (size_t)a.n_rows * a.n_cols, kBcApplyObject)) return;
     if (a.combine == 0) {
       a.object[gi] = safe_cdiv(num, den);
     } else {
@@ -2351,6 +2417,8 @@ extern "C" emg_status emg_step_minibatch_noalloc(float* object, int32_t n_rows, 
   sa.order = d_idx;
   sa.n_rows = n_rows;
   sa.n_cols = n_cols;
+  sa.n_pos = n_pos;
+  sa.b = b;
   sa.levels = p->levels;
   sa.prolong = p->prolong;
   sa.joint = p->joint;
@@ -2368,6 +2436,7 @@ extern "C" emg_status emg_step_minibatch_noalloc(float* object, int32_t n_rows, 
   aa.pos = pos;
   aa.order = d_idx;
   aa.b = b;
+  aa.n_pos = n_pos;
   aa.n_rows = n_rows;
   aa.n_cols = n_cols;
   aa.m = m;

@@ -19,3 +19,14 @@ def lib():
     import paper_2511_01793_gb300 as emg
     emg.load()
     return emg
+
+
+@pytest.fixture(autouse=True)
+def _bounds_check_clean(request):
+    """In the bounds-check build (EMG_BUILD_VARIANT=boundscheck) every GPU test
+    must leave the kernels' index-check error word clear."""
+    yield
+    if os.environ.get("EMG_BUILD_VARIANT") == "boundscheck" and request.node.get_closest_marker("gpu"):
+        import paper_2511_01793_gb300 as emg
+
+        assert emg.emg_debug_bounds_errors() == 0
