@@ -63,6 +63,11 @@ struct emg_ctx {
   double* d_scalar = nullptr;     // [64] assorted scalar results
   double* d_norm = nullptr;       // [1024] normalisation partials
   unsigned* d_mq = nullptr;       // [2] max|Q|^2 slots (float bits), alternating per minibatch
+  // Fused probe prep (cluster step kernels, FFT path): [0] tickets, [1] prep
+  // tiles done, [2] bounded wait gave up.  Both counters grow across the
+  // launches that follow a max|Q|^2 seed; the host keeps their expected values.
+  unsigned* d_sync = nullptr;
+  unsigned ticket_base = 0, prep_done_base = 0;
   int32_t* d_epoch_order = nullptr;  // [N] order read by the captured epoch graph
 
   // One epoch captured as a CUDA graph (replayed per epoch on `stream`), and
@@ -127,6 +132,10 @@ struct emg_batch {
   int* d_epoch = nullptr;         // current epoch within the call
   std::string err;
 };
+
+#ifndef EMG_FUSE_PREP
+#define EMG_FUSE_PREP 1  // probe prep inside the cluster step launch (0: always a separate kernel)
+#endif
 
 namespace {
 
@@ -260,6 +269,7 @@ void free_all(emg_ctx* c) {
   cudaFree(c->d_scalar);
   cudaFree(c->d_norm);
   cudaFree(c->d_mq);
+  cudaFree(c->d_sync);
   cudaFree(c->d_epoch_order);
   if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
   if (c->sgraph.exec) cudaGraphExecDestroy(c->sgraph.exec);
@@ -382,6 +392,8 @@ void permutation(uint64_t seed, int64_t epoch, int32_t n, int32_t* out) {
 // Seeds max|Q|^2 of the bound probe into slot 0 before a call's first minibatch.
 emg_status seed_probe_max(emg_ctx* c, cudaStream_t s) {
   EMG_CUDA(c, cudaMemsetAsync(c->d_mq, 0, 2 * sizeof(unsigned), s));
+  EMG_CUDA(c, cudaMemsetAsync(c->d_sync, 0, 2 * sizeof(unsigned), s));
+  c->ticket_base = c->prep_done_base = 0;
   LaunchMark mk(c, kKindOther);
   cudaError_t e = emg::launch_probe_max(c->probe, c->m, c->d_mq, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "k_probe_max launch");
@@ -407,11 +419,17 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
     if (e != cudaSuccess) return cuda_fail(c, e, "k_amp_gather launch");
     EMG_CUDA(c, cudaEventRecord(c->ev_side, c->side));
   }
-  {
-    LaunchMark mk(c, kKindPrep);
-    e = emg::launch_prep(pa, strm);
+  // The probe prep runs inside the cluster step launch where it fits (FFT path),
+  // beside the gather and transforms; otherwise as its own kernel before it.
+  PrepArgs pf = pa;
+  const int fused_tiles = (EMG_FUSE_PREP && !c->tc && c->cluster >= 2) ? emg::fused_prep_tiles(pf, c->m, c->cluster) : 0;
+  if (fused_tiles == 0) {
+    {
+      LaunchMark mk(c, kKindPrep);
+      e = emg::launch_prep(pa, strm);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "k_prep launch");
   }
-  if (e != cudaSuccess) return cuda_fail(c, e, "k_prep launch");
   if (c->stream_src) EMG_CUDA(c, cudaStreamWaitEvent(strm, c->ev_side, 0));
   StepArgs sa{};
   sa.object = c->object;
@@ -441,6 +459,16 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   const bool atomic = c->par.scatter == EMG_SCATTER_ATOMIC;
   sa.s_num = atomic ? c->d_snum : nullptr;
   sa.s_den = atomic ? c->d_sden : nullptr;
+  sa.sync = c->d_sync;
+  if (fused_tiles > 0) {
+    sa.prep = pf;
+    sa.prep_tiles = fused_tiles;
+    sa.prep_clusters = (fused_tiles + c->cluster - 1) / c->cluster;
+    sa.ticket_base = c->ticket_base;
+    sa.prep_target = c->prep_done_base + (unsigned)fused_tiles;
+    c->ticket_base += (unsigned)(b + sa.prep_clusters);
+    c->prep_done_base += (unsigned)fused_tiles;
+  }
   if (c->tc) {
     emg::TcStepArgs ta{};
     ta.object = c->object;
@@ -501,6 +529,12 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
 // Reads (synchronously) the flag the tensor-core kernels set when one of their
 // bounded waits gave up; callers invoke it where they synchronise anyway.
 emg_status check_tc_flag(emg_ctx* c) {
+  unsigned gave_up = 0;
+  EMG_CUDA(c, cudaMemcpy(&gave_up, c->d_sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (gave_up) {
+    EMG_CUDA(c, cudaMemset(c->d_sync + 2, 0, sizeof(unsigned)));
+    return fail(c, EMG_ETIMEOUT, "the step kernel's bounded wait for the fused probe prep gave up");
+  }
   if (!c->tc) return EMG_OK;
   int flag = 0;
   EMG_CUDA(c, cudaMemcpy(&flag, emg::tc_error_flag(c->tc), sizeof(int), cudaMemcpyDeviceToHost));
@@ -903,7 +937,7 @@ emg_status emg_create(emg_ctx** out, const emg_problem* pr, const emg_params* pa
       dmalloc(&c->d_zt, (size_t)B * mm) || dmalloc(&c->d_qt, (size_t)B * mm) ||
       dmalloc(&c->d_mu, (size_t)B) || dmalloc(&c->d_phi, (size_t)N) ||
       dmalloc(&c->d_phi_after, (size_t)B) || dmalloc(&c->d_partial, (size_t)N) ||
-      dmalloc(&c->d_scalar, (size_t)64) || dmalloc(&c->d_norm, (size_t)1024) || dmalloc(&c->d_mq, (size_t)2) ||
+      dmalloc(&c->d_scalar, (size_t)64) || dmalloc(&c->d_norm, (size_t)1024) || dmalloc(&c->d_mq, (size_t)2) || dmalloc(&c->d_sync, (size_t)4) ||
       dmalloc(&c->d_epoch_order, (size_t)N) ||
       dmalloc(&c->d_wq, mm))
     return bail(EMG_ENOMEM);
@@ -938,6 +972,7 @@ emg_status emg_create(emg_ctx** out, const emg_problem* pr, const emg_params* pa
   if (cudaMemsetAsync(c->d_phi_after, 0xff, (size_t)B * sizeof(double), c->stream) != cudaSuccess)
     return bail(EMG_ECUDA);
   c->cap_minibatch = B;
+  if (cudaMemsetAsync(c->d_sync, 0, 4 * sizeof(unsigned), c->stream) != cudaSuccess) return bail(EMG_ECUDA);
   if (set_intensity_impl(c, pr->intensity) != EMG_OK) return bail(EMG_ECUDA);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(EMG_ECUDA);
   *out = c;
@@ -1461,6 +1496,7 @@ emg_status emg_autotune(emg_ctx* c, int32_t* chosen, double* ms_per_minibatch) {
     c->probe = tq;
     if ((st = ensure_orders(c, (size_t)c->n_pos)) != EMG_OK) break;
     cudaMemcpyAsync(c->d_orders, idx.data(), B * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+    st = seed_probe_max(c, c->stream);
     for (int r = 0; r < 2 && st == EMG_OK; ++r) st = enqueue_minibatch(c, c->d_orders, B, c->d_phi, r, c->stream);
     cudaEventRecord(e0, c->stream);
     const int reps = 6;

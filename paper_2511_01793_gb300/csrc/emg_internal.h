@@ -84,6 +84,16 @@ struct StepArgs {
   const float2* r_in;           // [b][m][m] natural order, or null (FFT path)
   const double* r_partial;      // [b][r_tiles] sums of (|Psi| - a)^2
   int r_tiles;
+  // Probe prep fused into the launch (prep_clusters > 0, cluster kernels on the
+  // FFT path): every cluster takes a ticket (sync[0] - ticket_base) when it
+  // starts; tickets below prep_clusters compute the tiles of `prep`, the rest
+  // take the minibatch's positions in ticket order and, before the multigrid
+  // phase, wait (bounded) until sync[1] reaches prep_target.  Both counters
+  // grow across the launches of an epoch and are zeroed with max|Q|^2.
+  PrepArgs prep;
+  int prep_clusters, prep_tiles;
+  unsigned ticket_base, prep_target;
+  unsigned* sync;               // [0] tickets, [1] prep tiles done, [2] wait gave up (error flag)
 };
 
 struct ApplyArgs {
@@ -161,6 +171,9 @@ cudaError_t launch_amp_prep(const float* d, float* amp, int m, int n_pos, cudaSt
 // a_k of positions idx[0..b) (device indices) from d, which may be mapped host memory.
 cudaError_t launch_amp_gather(const float* d, const int32_t* idx, int b, float* amp, int m, cudaStream_t s);
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
+// Fused probe prep for the cluster step kernel: sets a.tile / a.halo for it
+// and returns its tile count, or 0 when it does not fit beside the step.
+int fused_prep_tiles(PrepArgs& a, int m, int cluster);
 cudaError_t launch_probe_max(const float2* probe, int m, unsigned* slot, cudaStream_t s);
 // Fills tile/halo of a and returns true when the tiled prep fits in shared memory.
 bool prep_tiled_config(PrepArgs& a);

@@ -391,6 +391,21 @@ __global__ void __launch_bounds__(256) k_probe_max(const float2* __restrict__ pr
 // shared memory and writes the level arrays of its own pixels.
 constexpr int kPrepTileThreads = 256;
 
+// Bounded wait of the fused prep: 1 s of %globaltimer, then the error flag.
+constexpr unsigned long long kFusedPrepWaitNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 struct PrepRegion {
   int lo_r, lo_c, h, w;   // region of one level, in that level's pixels
 };
@@ -419,16 +434,14 @@ __device__ __forceinline__ T prolong_region(const T* y, const PrepRegion& g, int
                   y[(i2 - g.lo_r) * g.w + (j2 - g.lo_c)]);
 }
 
-__global__ void __launch_bounds__(kPrepTileThreads) k_prep_tile(const PrepArgs a) {
-  extern __shared__ float2 smp[];
-  const int tid = threadIdx.x;
+// The probe-only arrays of one tile (index `t`) of the probe, computed by
+// `nt` threads of a CTA with `smp` as shared scratch (prep_tile_smem bytes).
+__device__ __forceinline__ void prep_tile_body(const PrepArgs& a, int t, int tid, int nt, float2* smp) {
   const int m = a.m, L = a.levels, tile = a.tile, halo = a.halo;
   const int tiles_per_row = m / tile;
-  const int R0 = (blockIdx.x / tiles_per_row) * tile, C0 = (blockIdx.x % tiles_per_row) * tile;
-  pdl_trigger();
-  pdl_wait();  // the probe and max|Q|^2 come from the previous combine
+  const int R0 = (t / tiles_per_row) * tile, C0 = (t % tiles_per_row) * tile;
   const float MQ = __uint_as_float(*a.mq_read);
-  if (blockIdx.x == 0 && tid == 0) *a.mq_next = 0u;
+  if (t == 0 && tid == 0) *a.mq_next = 0u;
 
   // carve shared memory: per level Q_l (float2), u_l (float), T_l (float, level l+1 region)
   float2* Qs[kMaxLevels];
@@ -454,7 +467,7 @@ __global__ void __launch_bounds__(kPrepTileThreads) k_prep_tile(const PrepArgs a
   // level 0
   {
     const PrepRegion g = prep_region(m, R0, C0, tile, halo, 0);
-    for (int p = tid; p < g.h * g.w; p += kPrepTileThreads) {
+    for (int p = tid; p < g.h * g.w; p += nt) {
       const int r = g.lo_r + p / g.w, c = g.lo_c + p % g.w;
       const float2 q = a.probe[r * m + c];
       const float a2 = cabs2(q);
@@ -474,7 +487,7 @@ __global__ void __launch_bounds__(kPrepTileThreads) k_prep_tile(const PrepArgs a
     const int mf = m >> l, mc = mf >> 1;
     const int tr0 = R0 >> (l + 1), tc0 = C0 >> (l + 1), tsz = tile >> (l + 1);
     // coarse: T = I_h^H |Q_l|^2, Q_{l+1} = I_h^H Q_l, u_{l+1} = W_u^H I_h^H u_l, G_{l+1}
-    for (int p = tid; p < gc.h * gc.w; p += kPrepTileThreads) {
+    for (int p = tid; p < gc.h * gc.w; p += nt) {
       const int i = p / gc.w, j = p % gc.w;
       float t = 0.f, ur = 0.f;
       float2 qs = czero();
@@ -505,7 +518,7 @@ __global__ void __launch_bounds__(kPrepTileThreads) k_prep_tile(const PrepArgs a
     __syncthreads();
     // fine weights of the tile's level-l pixels: W_z = |Q_l|^2 / S, W_R = (I_H^h Q_{l+1}) conj(Q_l) / S
     const int fr0 = R0 >> l, fc0 = C0 >> l, fsz = tile >> l;
-    for (int p = tid; p < fsz * fsz; p += kPrepTileThreads) {
+    for (int p = tid; p < fsz * fsz; p += nt) {
       const int r = fr0 + p / fsz, c = fc0 + p % fsz;
       const float S = prolong_region<float>(Ts[l], gc, mc, r, c, a.prolong);
       const float2 pq = prolong_region<float2>(Qs[l + 1], gc, mc, r, c, a.prolong);
@@ -514,6 +527,13 @@ __global__ void __launch_bounds__(kPrepTileThreads) k_prep_tile(const PrepArgs a
       a.WR[l][r * mf + c] = safe_cdiv(cmulc(pq, q), S);
     }
   }
+}
+
+__global__ void __launch_bounds__(kPrepTileThreads) k_prep_tile(const PrepArgs a) {
+  extern __shared__ float2 smp[];
+  pdl_trigger();
+  pdl_wait();  // the probe and max|Q|^2 come from the previous combine
+  prep_tile_body(a, blockIdx.x, threadIdx.x, kPrepTileThreads, smp);
 }
 
 __host__ size_t prep_tile_smem(const PrepArgs& a) {
@@ -852,8 +872,34 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
   __shared__ double xd[C], xd2[C];
   __shared__ double redd[2];
   __shared__ float redf[NT / 32];
+  __shared__ int ticket_sh;
   const int tid = threadIdx.x;
-  const int kb = blockIdx.x / C;
+  int kb = blockIdx.x / C;
+  if constexpr (!RIN) {
+    if (a.prep_clusters > 0) {
+      // role by ticket, taken before this launch lets the next one start: a
+      // cluster only ever waits for clusters that started before it
+      if (rank == 0 && tid == 0) ticket_sh = (int)(atomicAdd(a.sync, 1u) - a.ticket_base);
+      cl.sync();  // every CTA of the cluster is running; rank 0's ticket is visible
+      const int t = *cl.map_shared_rank(&ticket_sh, 0);
+      if (t < a.prep_clusters) {
+        pdl_trigger();
+        pdl_wait();  // the probe and max|Q|^2 come from the previous combine
+        const int tile = t * C + rank;
+        if (tile < a.prep_tiles) {
+          prep_tile_body(a.prep, tile, tid, NT, sm);
+          __syncthreads();
+          if (tid == 0) {
+            __threadfence();
+            atomicAdd(a.sync + 1, 1u);
+          }
+        }
+        cl.sync();  // no CTA leaves while a peer may still read rank 0's ticket
+        return;
+      }
+      kb = t - a.prep_clusters;
+    }
+  }
   int k = a.order[kb];
   if (!EMG_INB(k, a.n_pos, kBcOrder)) k = 0;
   const bool slot_ok = EMG_INB(kb, a.b, kBcPatchWrite);
@@ -952,6 +998,21 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
   __syncthreads();
   }  // !RIN
 
+  if constexpr (!RIN) {
+    if (a.prep_clusters > 0 && a.levels > 1) {
+      // the level arrays of this minibatch come from the prep clusters of this launch
+      if (tid == 0) {
+        const unsigned long long t0 = globaltimer_ns();
+        while (ld_acquire_u32(a.sync + 1) < a.prep_target) {
+          if (globaltimer_ns() - t0 > kFusedPrepWaitNs) {
+            atomicExch(a.sync + 2, 1u);
+            break;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
   // a5: MAGPIE multigrid on row slabs; level-l buffers (l >= 1) reuse colbuf.
   // Z_l keeps one halo row above and below my rows for the prolongation.
   float2* Zl[kMaxLevels];
@@ -999,8 +1060,8 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
           for (int dx = 0; dx < 2; ++dx) {
             const int lr = 2 * i + dy, r = row0 + lr, c = 2 * j + dx;
             const float2 zk = zbuf[lr * M + c];
-            zs = cadd(zs, cscale(zk, Wz[r * M + c]));
-            rs = cadd(rs, cmul(WR[r * M + c], rowbuf[lr * SR + c]));
+            zs = cadd(zs, cscale(zk, __ldcg(Wz + r * M + c)));
+            rs = cadd(rs, cmul(__ldcg(WR + r * M + c), rowbuf[lr * SR + c]));
           }
         Z1w[i * sc + j] = cscale(zs, 0.25f);
         R1w[i * sc + j] = cscale(rs, 0.25f);
@@ -1024,8 +1085,8 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
           for (int dx = 0; dx < 2; ++dx) {
             const int lr = 2 * i + dy, r = rank * hf + lr, c = 2 * j + dx;
             const int wi = EMG_INB(r * wf + c, wf * wf, kBcLevel) ? r * wf + c : 0;
-            zs = cadd(zs, cscale(Zf[lr * sf + c], Wz[wi]));
-            rs = cadd(rs, cmul(WR[wi], Rf[lr * sf + c]));
+            zs = cadd(zs, cscale(Zf[lr * sf + c], __ldcg(Wz + wi)));
+            rs = cadd(rs, cmul(__ldcg(WR + wi), Rf[lr * sf + c]));
           }
         Zc[i * sc + j] = cscale(zs, 0.25f);
         Rc[i * sc + j] = cscale(rs, 0.25f);
@@ -1043,7 +1104,7 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
         const int i = p / wl, j = p % wl, gi = rank * hl + i;
         const int li = EMG_INB(gi * wl + j, wl * wl, kBcLevel) ? gi * wl + j : 0;
         const float2 z = Zw[i * sl + j];
-        Zw[i * sl + j] = cmul(G[li], csub(Rw[i * sl + j], cmul(Q[li], z)));
+        Zw[i * sl + j] = cmul(__ldcg(G + li), csub(Rw[i * sl + j], cmul(__ldcg(Q + li), z)));
       }
     }
     // back up: c_l = I_H^h c_{l+1} + G_l (R_l - Q_l (z_l + I_H^h c_{l+1}))
@@ -1065,7 +1126,7 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
         const int li = EMG_INB(gi * wl + j, wl * wl, kBcLevel) ? gi * wl + j : 0;
         const float2 pro = prolong_halo<float2>(Zc, sc, wc, i, j, a.prolong);
         const float2 zp = cadd(Zw[i * sl + j], pro);
-        Zw[i * sl + j] = cadd(pro, cmul(G[li], csub(Rw[i * sl + j], cmul(Q[li], zp))));
+        Zw[i * sl + j] = cadd(pro, cmul(__ldcg(G + li), csub(Rw[i * sl + j], cmul(__ldcg(Q + li), zp))));
       }
     }
     if (halo) {
@@ -1907,6 +1968,33 @@ bool prep_tiled_config(PrepArgs& a) {
   return prep_tile_smem(a) <= kPrepTileSmemMax;
 }
 
+template <int M, int C>
+constexpr size_t stepc_smem_bytes() {
+  return CTile<M, C>::smem_elems * sizeof(float2);
+}
+
+int fused_prep_tiles(PrepArgs& a, int m, int cluster) {
+  size_t smem = 0;
+  switch (m * 16 + cluster) {
+    case 16 * 16 + 2: smem = stepc_smem_bytes<16, 2>(); break;
+    case 32 * 16 + 2: smem = stepc_smem_bytes<32, 2>(); break;
+    case 64 * 16 + 2: smem = stepc_smem_bytes<64, 2>(); break;
+    case 64 * 16 + 4: smem = stepc_smem_bytes<64, 4>(); break;
+    case 128 * 16 + 2: smem = stepc_smem_bytes<128, 2>(); break;
+    case 128 * 16 + 4: smem = stepc_smem_bytes<128, 4>(); break;
+    case 128 * 16 + 8: smem = stepc_smem_bytes<128, 8>(); break;
+    case 256 * 16 + 8: smem = stepc_smem_bytes<256, 8>(); break;
+    default: return 0;
+  }
+  int tile = 32;
+  while (tile < (1 << (a.levels - 1))) tile *= 2;
+  if (tile > m) tile = m;
+  a.tile = tile;
+  a.halo = (a.prolong == 1) ? (1 << (a.levels - 1)) : 0;
+  if ((tile >> (a.levels - 1)) < 1 || prep_tile_smem(a) > smem) return 0;
+  return (m / tile) * (m / tile);
+}
+
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
   PrepArgs t = a;
   if (a.mq_read && prep_tiled_config(t)) {
@@ -2043,8 +2131,8 @@ cudaError_t set_cluster_attrs() {
 template <int M, int C>
 cudaError_t launch_stepc_t(int b, const StepArgs& a, cudaStream_t s) {
   using TL = CTile<M, C>;
-  cudaError_t e = launch_cluster_pdl(k_stepc<M, C>, C, dim3(C * b), dim3(TL::NT), TL::smem_elems * sizeof(float2),
-                                     s, a);
+  cudaError_t e = launch_cluster_pdl(k_stepc<M, C>, C, dim3(C * (b + a.prep_clusters)), dim3(TL::NT),
+                                     TL::smem_elems * sizeof(float2), s, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
