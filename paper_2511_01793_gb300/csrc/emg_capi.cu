@@ -68,6 +68,7 @@ struct emg_ctx {
   // launches that follow a max|Q|^2 seed; the host keeps their expected values.
   unsigned* d_sync = nullptr;
   unsigned ticket_base = 0, prep_done_base = 0;
+  int resident_cluster = -1, resident_clusters = 0;  // step clusters resident at once, for `cluster`
   int32_t* d_epoch_order = nullptr;  // [N] order read by the captured epoch graph
 
   // One epoch captured as a CUDA graph (replayed per epoch on `stream`), and
@@ -419,10 +420,19 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
     if (e != cudaSuccess) return cuda_fail(c, e, "k_amp_gather launch");
     EMG_CUDA(c, cudaEventRecord(c->ev_side, c->side));
   }
-  // The probe prep runs inside the cluster step launch where it fits (FFT path),
-  // beside the gather and transforms; otherwise as its own kernel before it.
+  // The probe prep runs inside the cluster step launch (FFT path) when the
+  // launch fits in one wave of resident clusters: there it overlaps the gather
+  // and transforms.  Otherwise it is its own kernel before the step.
   PrepArgs pf = pa;
-  const int fused_tiles = (EMG_FUSE_PREP && !c->tc && c->cluster >= 2) ? emg::fused_prep_tiles(pf, c->m, c->cluster) : 0;
+  int fused_tiles = (EMG_FUSE_PREP && !c->tc && c->cluster >= 2) ? emg::fused_prep_tiles(pf, c->m, c->cluster) : 0;
+  if (fused_tiles > 0) {
+    const int prep_clusters = (fused_tiles + c->cluster - 1) / c->cluster;
+    if (c->resident_cluster != c->cluster) {
+      c->resident_clusters = emg::step_resident_clusters(c->m, c->cluster);
+      c->resident_cluster = c->cluster;
+    }
+    if (b + prep_clusters > c->resident_clusters) fused_tiles = 0;
+  }
   if (fused_tiles == 0) {
     {
       LaunchMark mk(c, kKindPrep);

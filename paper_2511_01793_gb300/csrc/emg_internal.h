@@ -174,6 +174,8 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 // Fused probe prep for the cluster step kernel: sets a.tile / a.halo for it
 // and returns its tile count, or 0 when it does not fit beside the step.
 int fused_prep_tiles(PrepArgs& a, int m, int cluster);
+// Step-kernel clusters that can be resident on the device at once (0 if unknown).
+int step_resident_clusters(int m, int cluster);
 cudaError_t launch_probe_max(const float2* probe, int m, unsigned* slot, cudaStream_t s);
 // Fills tile/halo of a and returns true when the tiled prep fits in shared memory.
 bool prep_tiled_config(PrepArgs& a);

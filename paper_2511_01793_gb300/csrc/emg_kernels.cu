@@ -1973,6 +1973,35 @@ constexpr size_t stepc_smem_bytes() {
   return CTile<M, C>::smem_elems * sizeof(float2);
 }
 
+// Clusters of the step kernel that can be resident at once (CTAs per SM from
+// the occupancy calculator x SMs / cluster size), or 0 if unknown.
+template <int M, int C>
+int stepc_resident_clusters() {
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stepc<M, C>, CTile<M, C>::NT,
+                                                    stepc_smem_bytes<M, C>()) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * sms / C;
+}
+
+int step_resident_clusters(int m, int cluster) {
+  switch (m * 16 + cluster) {
+    case 16 * 16 + 2: return stepc_resident_clusters<16, 2>();
+    case 32 * 16 + 2: return stepc_resident_clusters<32, 2>();
+    case 64 * 16 + 2: return stepc_resident_clusters<64, 2>();
+    case 64 * 16 + 4: return stepc_resident_clusters<64, 4>();
+    case 128 * 16 + 2: return stepc_resident_clusters<128, 2>();
+    case 128 * 16 + 4: return stepc_resident_clusters<128, 4>();
+    case 128 * 16 + 8: return stepc_resident_clusters<128, 8>();
+    case 256 * 16 + 8: return stepc_resident_clusters<256, 8>();
+    default: return 0;
+  }
+}
+
 int fused_prep_tiles(PrepArgs& a, int m, int cluster) {
   size_t smem = 0;
   switch (m * 16 + cluster) {
