@@ -358,6 +358,15 @@ emg_status emg_debug_bounds_selftest(uint32_t* mask);
 emg_status emg_set_cluster(emg_ctx* ctx, int32_t cluster);
 
 /*
+ * Where the probe prep of a minibatch runs: 1 (the default) inside the step
+ * launch of the cluster kernels, beside the gather and transforms, when the
+ * launch fits in one wave of resident clusters; 0 always as its own kernel
+ * before the step.  Speed only: the results are identical.  Synchronises.
+ * EMG_EINVAL for other values.
+ */
+emg_status emg_set_prep_fusion(emg_ctx* ctx, int32_t enable);
+
+/*
  * Autotuner: times a few minibatches (on private copies of the bound state,
  * which is left untouched) for every valid FFT tiling and keeps the fastest.
  * chosen (host, or NULL) receives it, ms_per_minibatch (host, or NULL) its

@@ -69,6 +69,7 @@ struct emg_ctx {
   unsigned* d_sync = nullptr;
   unsigned ticket_base = 0, prep_done_base = 0;
   int resident_cluster = -1, resident_clusters = 0;  // step clusters resident at once, for `cluster`
+  int fuse_prep = 1;              // probe prep inside the step launch where it fits (emg_set_prep_fusion)
   int32_t* d_epoch_order = nullptr;  // [N] order read by the captured epoch graph
 
   // One epoch captured as a CUDA graph (replayed per epoch on `stream`), and
@@ -133,10 +134,6 @@ struct emg_batch {
   int* d_epoch = nullptr;         // current epoch within the call
   std::string err;
 };
-
-#ifndef EMG_FUSE_PREP
-#define EMG_FUSE_PREP 1  // probe prep inside the cluster step launch (0: always a separate kernel)
-#endif
 
 namespace {
 
@@ -424,7 +421,7 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   // launch fits in one wave of resident clusters: there it overlaps the gather
   // and transforms.  Otherwise it is its own kernel before the step.
   PrepArgs pf = pa;
-  int fused_tiles = (EMG_FUSE_PREP && !c->tc && c->cluster >= 2) ? emg::fused_prep_tiles(pf, c->m, c->cluster) : 0;
+  int fused_tiles = (c->fuse_prep && !c->tc && c->cluster >= 2) ? emg::fused_prep_tiles(pf, c->m, c->cluster) : 0;
   if (fused_tiles > 0) {
     const int prep_clusters = (fused_tiles + c->cluster - 1) / c->cluster;
     if (c->resident_cluster != c->cluster) {
@@ -1341,6 +1338,18 @@ emg_status emg_set_gradient_chunk(emg_ctx* c, int32_t positions) {
   c->d_gz = c->d_gq = nullptr;
   c->grad_chunk_req = positions;
   c->grad_chunk = 0;
+  return EMG_OK;
+}
+
+emg_status emg_set_prep_fusion(emg_ctx* c, int32_t enable) {
+  if (!c) return EMG_EINVAL;
+  if (enable != 0 && enable != 1) return fail(c, EMG_EINVAL, "enable must be 0 or 1");
+  if (enable != c->fuse_prep) {
+    DeviceGuard g(c->device);
+    EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->fuse_prep = enable;
+    drop_graphs(c);
+  }
   return EMG_OK;
 }
 

@@ -252,3 +252,23 @@ def test_autotune_search_chooses_b_tiling_and_scatter(lib, torch):
         lib.emg_autotune_search(c.ctx, minibatch=(4,), trial_epochs=0)
     c.close()
     ref.close()
+
+
+@pytest.mark.parametrize("m,levels,prolong,cl", [(64, 3, "bilinear", 2), (128, 3, "bilinear", 4),
+                                                  (128, 2, "const", 8), (128, 7, "const", 2)])
+def test_fused_probe_prep_equals_the_separate_kernel(lib, torch, m, levels, prolong, cl):
+    """The probe prep inside the step launch (ticket-ordered prep clusters) gives
+    bitwise the results of the prep as its own kernel, over graph-replayed epochs
+    and single minibatches."""
+    case = Case(n=2 * m + 40, m=m, side=5, noise_peak=1e4, seed=95 + m + levels)
+    p = oracle_params(minibatch=7, levels=levels, prolong=prolong)
+    out = []
+    for fuse in (1, 0):
+        c = make_context(lib, case, p, seed=3)
+        lib.emg_set_cluster(c.ctx, cl)
+        lib.emg_set_prep_fusion(c.ctx, fuse)
+        lib.emg_run_epochs(c.ctx, 2)
+        lib.emg_step_minibatch(c.ctx, [0, 3, 5])
+        out.append(state(c))
+        c.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
