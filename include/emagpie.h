@@ -367,6 +367,15 @@ emg_status emg_set_cluster(emg_ctx* ctx, int32_t cluster);
 emg_status emg_set_prep_fusion(emg_ctx* ctx, int32_t enable);
 
 /*
+ * Test hook for the failure path of the fused prep's wait: each later step
+ * launch waits for `extra` more prep tiles than it has, so its bounded wait
+ * (1 s) runs out, sets the device flag and the kernel goes on; the next call
+ * that synchronises returns EMG_ETIMEOUT.  0 (the default) restores normal
+ * operation.  Synchronises.
+ */
+emg_status emg_debug_prep_wait_extra(emg_ctx* ctx, uint32_t extra);
+
+/*
  * Autotuner: times a few minibatches (on private copies of the bound state,
  * which is left untouched) for every valid FFT tiling and keeps the fastest.
  * chosen (host, or NULL) receives it, ms_per_minibatch (host, or NULL) its

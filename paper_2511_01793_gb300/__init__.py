@@ -27,7 +27,7 @@ __all__ = [
     "emg_step_minibatch", "emg_position_stats", "emg_set_verify", "emg_run_epochs", "emg_misfit",
     "emg_set_epoch", "emg_schedule_permutation", "emg_stopping_epoch", "emg_run_until", "emg_reconstruct_host",
     "emg_simulate_intensity", "emg_fft2", "emg_dft2_bf16x3", "emg_step_minibatch_noalloc", "emg_misfit_gradient",
-    "emg_set_cluster", "emg_set_prep_fusion", "emg_set_gradient_chunk", "emg_autotune", "emg_set_minibatch", "emg_set_scatter",
+    "emg_set_cluster", "emg_set_prep_fusion", "emg_debug_prep_wait_extra", "emg_set_gradient_chunk", "emg_autotune", "emg_set_minibatch", "emg_set_scatter",
     "emg_selftest_bounded_wait", "emg_debug_fail_alloc", "emg_debug_bounds_errors",
     "emg_debug_bounds_selftest",
     "emg_autotune_search", "EmgTuneRequest", "EmgTuneResult", "emg_batch_create", "emg_batch_run_epochs", "emg_batch_destroy",
@@ -109,6 +109,7 @@ _SIGS = {
     "emg_misfit_gradient": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _F64P]),
     "emg_set_cluster": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "emg_set_prep_fusion": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "emg_debug_prep_wait_extra": (ctypes.c_int, [_VP, ctypes.c_uint32]),
     "emg_set_gradient_chunk": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "emg_autotune": (ctypes.c_int, [_VP, _I32P, _F64P]),
     "emg_set_minibatch": (ctypes.c_int, [_VP, ctypes.c_int32]),
@@ -345,6 +346,11 @@ def emg_set_gradient_chunk(ctx: int, positions: int) -> None:
 
 def emg_set_prep_fusion(ctx: int, enable: bool) -> None:
     _check(load().emg_set_prep_fusion(ctx, int(bool(enable))), "emg_set_prep_fusion", ctx)
+
+
+def emg_debug_prep_wait_extra(ctx: int, extra: int) -> None:
+    """Test hook: later step launches wait for `extra` prep tiles that never come (0: off)."""
+    _check(load().emg_debug_prep_wait_extra(ctx, extra), "emg_debug_prep_wait_extra", ctx)
 
 
 def emg_set_cluster(ctx: int, cluster: int) -> None:

@@ -70,6 +70,7 @@ struct emg_ctx {
   unsigned ticket_base = 0, prep_done_base = 0;
   int resident_cluster = -1, resident_clusters = 0;  // step clusters resident at once, for `cluster`
   int fuse_prep = 1;              // probe prep inside the step launch where it fits (emg_set_prep_fusion)
+  unsigned prep_wait_extra = 0;   // test hook: added to the prep count a launch waits for
   int32_t* d_epoch_order = nullptr;  // [N] order read by the captured epoch graph
 
   // One epoch captured as a CUDA graph (replayed per epoch on `stream`), and
@@ -472,7 +473,7 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
     sa.prep_tiles = fused_tiles;
     sa.prep_clusters = (fused_tiles + c->cluster - 1) / c->cluster;
     sa.ticket_base = c->ticket_base;
-    sa.prep_target = c->prep_done_base + (unsigned)fused_tiles;
+    sa.prep_target = c->prep_done_base + (unsigned)fused_tiles + c->prep_wait_extra;
     c->ticket_base += (unsigned)(b + sa.prep_clusters);
     c->prep_done_base += (unsigned)fused_tiles;
   }
@@ -1338,6 +1339,15 @@ emg_status emg_set_gradient_chunk(emg_ctx* c, int32_t positions) {
   c->d_gz = c->d_gq = nullptr;
   c->grad_chunk_req = positions;
   c->grad_chunk = 0;
+  return EMG_OK;
+}
+
+emg_status emg_debug_prep_wait_extra(emg_ctx* c, uint32_t extra) {
+  if (!c) return EMG_EINVAL;
+  DeviceGuard g(c->device);
+  EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->prep_wait_extra = extra;
+  drop_graphs(c);
   return EMG_OK;
 }
 

@@ -115,6 +115,7 @@ def test_context_free_calls_validate_arguments(lib):
     assert lib.emg_autotune_search(None, None, None) == emg.EMG_EINVAL
     assert lib.emg_set_cluster(None, 2) == emg.EMG_EINVAL
     assert lib.emg_set_prep_fusion(None, 1) == emg.EMG_EINVAL
+    assert lib.emg_debug_prep_wait_extra(None, 0) == emg.EMG_EINVAL
     lib.emg_destroy(None)  # no-op
 
 

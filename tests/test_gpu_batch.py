@@ -272,3 +272,35 @@ def test_fused_probe_prep_equals_the_separate_kernel(lib, torch, m, levels, prol
         out.append(state(c))
         c.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_fused_prep_wait_gives_up_reports_and_recovers(lib, torch):
+    """The step kernel's bounded wait for the fused prep, made to run out (it waits
+    for prep tiles that never come): the call reports EMG_ETIMEOUT after about
+    1 s, and the context then runs exactly as a fresh one."""
+    import time
+
+    m = 128
+    case = Case(n=2 * m + 40, m=m, side=4, noise_peak=1e4, seed=99)
+    p = oracle_params(minibatch=6, levels=3, prolong="bilinear")
+    c = make_context(lib, case, p, seed=2)
+    lib.emg_debug_prep_wait_extra(c.ctx, 1000)
+    t0 = time.perf_counter()
+    with pytest.raises(lib.EmgError) as err:
+        lib.emg_step_minibatch(c.ctx, [0, 1, 2], want_misfit=True)
+    assert err.value.status == lib.EMG_ETIMEOUT
+    assert time.perf_counter() - t0 >= 0.9
+    lib.emg_debug_prep_wait_extra(c.ctx, 0)
+    # recovery: rebind the initial state and compare with a fresh context
+    c.obj.copy_(torch.from_numpy(case.z0.astype(np.complex64)))
+    c.probe.copy_(torch.from_numpy(case.q0.astype(np.complex64)))
+    torch.cuda.synchronize()
+    lib.emg_set_epoch(c.ctx, 0)
+    lib.emg_run_epochs(c.ctx, 2)
+    ref = make_context(lib, case, p, seed=2)
+    lib.emg_run_epochs(ref.ctx, 2)
+    z1, q1 = state(c)
+    z2, q2 = state(ref)
+    assert np.array_equal(z1, z2) and np.array_equal(q1, q2)
+    c.close()
+    ref.close()
