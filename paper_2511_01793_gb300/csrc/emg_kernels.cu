@@ -261,12 +261,15 @@ __global__ void __launch_bounds__(256) k_amp_prep(const float* __restrict__ d, f
 // device-readable address, e.g. pinned host memory).  A small grid that runs
 // beside the step kernels: each warp keeps kGatherRows rows of loads in flight.
 #ifndef EMG_GATHER_BLOCKS
-#define EMG_GATHER_BLOCKS 152
+#define EMG_GATHER_BLOCKS 38
 #endif
 #ifndef EMG_GATHER_ROWS
-#define EMG_GATHER_ROWS 2
+#define EMG_GATHER_ROWS 4
 #endif
-constexpr int kGatherRows = EMG_GATHER_ROWS, kGatherWarps = 4, kGatherBlocks = EMG_GATHER_BLOCKS;
+#ifndef EMG_GATHER_WARPS
+#define EMG_GATHER_WARPS 8
+#endif
+constexpr int kGatherRows = EMG_GATHER_ROWS, kGatherWarps = EMG_GATHER_WARPS, kGatherBlocks = EMG_GATHER_BLOCKS;
 template <int M>
 __global__ void __launch_bounds__(kGatherWarps * 32) k_amp_gather(const float* __restrict__ d,
                                                                  const int32_t* __restrict__ idx, int b,
