@@ -11,8 +11,8 @@ numpy's complex ``sqrt`` as the principal square root; everything else is
 written out per pixel with no blocking or fusion.  Positions within a
 minibatch are processed one at a time, in the given order.
 
-Readings where the paper is silent (all of them also listed in the design
-notes of the repository):
+Readings where the paper is silent, ambiguous or deviates (the CUDA library
+follows the same readings):
 
 * F is the unnormalised forward 2-D DFT and F^-1 carries 1/m^2 (Sec. 4.1: the
   dp_avg probe scaling equals the exit-wave norm only with this convention).
