@@ -86,6 +86,9 @@ struct emg_ctx {
   void* d_levels = nullptr;       // all multigrid arrays
   int32_t* d_orders = nullptr;    // [cap_orders]
   size_t cap_orders = 0;
+  int32_t* h_orders = nullptr;    // pinned staging of the order rows, [cap_h_orders]
+  size_t cap_h_orders = 0;
+  cudaEvent_t ev_orders = nullptr;  // the last copy out of h_orders
   double* d_hist = nullptr;       // [2][cap_hist]
   size_t cap_hist = 0;
   float* d_stage_d = nullptr;     // [N][m][m] intensity staging (host input path)
@@ -278,6 +281,9 @@ void free_all(emg_ctx* c) {
   cudaFree(c->d_wq);
   cudaFree(c->d_levels);
   cudaFree(c->d_orders);
+  if (c->ev_orders) cudaEventSynchronize(c->ev_orders);
+  if (c->h_orders) cudaFreeHost(c->h_orders);
+  if (c->ev_orders) cudaEventDestroy(c->ev_orders);
   cudaFree(c->d_hist);
   cudaFree(c->d_stage_d);
   cudaFree(c->d_own_object);
@@ -344,6 +350,25 @@ emg_status alloc_levels(emg_ctx* c) {
   pa.alpha = c->par.alpha;
   pa.w_eps = c->par.w_eps;
   pa.wq = c->d_wq;
+  return EMG_OK;
+}
+
+// Copies n order entries to d_orders through the pinned staging buffer (a
+// true asynchronous copy; the buffer is reused once the previous copy is done).
+emg_status upload_orders(emg_ctx* c, const int32_t* src, size_t n, cudaStream_t s) {
+  if (c->ev_orders) EMG_CUDA(c, cudaEventSynchronize(c->ev_orders));
+  if (n > c->cap_h_orders) {
+    if (c->h_orders) cudaFreeHost(c->h_orders);
+    c->h_orders = nullptr;
+    c->cap_h_orders = 0;
+    if (cudaMallocHost(&c->h_orders, n * sizeof(int32_t)) != cudaSuccess)
+      return fail(c, EMG_ENOMEM, "cudaMallocHost(orders) failed");
+    c->cap_h_orders = n;
+  }
+  memcpy(c->h_orders, src, n * sizeof(int32_t));
+  EMG_CUDA(c, cudaMemcpyAsync(c->d_orders, c->h_orders, n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  if (!c->ev_orders) EMG_CUDA(c, cudaEventCreateWithFlags(&c->ev_orders, cudaEventDisableTiming));
+  EMG_CUDA(c, cudaEventRecord(c->ev_orders, s));
   return EMG_OK;
 }
 
@@ -727,7 +752,7 @@ emg_status run_epochs_impl(emg_ctx* c, int32_t n_epochs, const int32_t* order, d
   emg_status st = ensure_orders(c, h.size());
   if (st != EMG_OK) return st;
   if ((st = ensure_hist(c, n_epochs)) != EMG_OK) return st;
-  EMG_CUDA(c, cudaMemcpyAsync(c->d_orders, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  if ((st = upload_orders(c, h.data(), h.size(), c->stream)) != EMG_OK) return st;
   // Profiling times each launch with events, so it runs the epochs as direct
   // launches; otherwise each epoch replays the captured graph.
   const bool use_graph = !c->profile;
@@ -1023,7 +1048,7 @@ emg_status emg_step_minibatch(emg_ctx* c, const int32_t* idx, int32_t b, double*
     if (idx[i] < 0 || idx[i] >= c->n_pos) return fail(c, EMG_EINVAL, "idx entry out of range");
   DeviceGuard g(c->device);
   if ((st = ensure_orders(c, (size_t)c->n_pos)) != EMG_OK) return st;
-  EMG_CUDA(c, cudaMemcpyAsync(c->d_orders, idx, (size_t)b * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  if ((st = upload_orders(c, idx, (size_t)b, c->stream)) != EMG_OK) return st;
   if ((st = seed_probe_max(c, c->stream)) != EMG_OK) return st;
   if ((st = enqueue_minibatch(c, c->d_orders, b, c->d_phi, 0, c->stream)) != EMG_OK) return st;
   c->last_b = b;
