@@ -5,9 +5,9 @@ Workload (one "step" = one eMAGPIE epoch over all scan positions): object
 512 x 512 complex, probe 128 x 128, 900 scan positions (30 x 30 raster, step
 12 px, +-2 px jitter), Poisson noise at 1e4 photons peak, 3 multigrid levels
 with 2x averaging restriction and bilinear prolongation, minibatch 64,
-alpha 0.05.  Inputs are synthetic and seeded (``synth``); intensities are
-simulated by the library's own forward model, then Poisson-sampled on the
-host.  The L2 cache (129 MB) is flushed by writing a 256 MB buffer before
+alpha 0.05.  Inputs are synthetic and seeded (``synth``): the simulated
+measurement of the true object and probe, Poisson-sampled on the host, the
+same arrays in both arms.  The L2 cache (129 MB) is flushed by writing a 256 MB buffer before
 every timed step; inputs are resident in HBM when a step starts.
 
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead
@@ -62,7 +62,8 @@ def parse_args():
     return ap.parse_args()
 
 
-def workload_config():
+def workload_config(world: int = 1):
+    """The workload description, identical in the GPU and the reference arm."""
     p = synth.CONFIGS[WORKLOAD]
     n_pos = p["side"] ** 2
     return {
@@ -73,7 +74,17 @@ def workload_config():
         "n": p["n"], "m": p["m"], "n_pos": n_pos, "minibatch": p["minibatch"],
         "levels": p["levels"], "prolong": p["prolong"], "alpha": p["alpha"],
         "l2": "flushed (256 MB write) before every timed step",
+        "intensities": "synth.measure_intensities of the true object and probe, Poisson-sampled "
+                       "(synth.poisson_noise, seed noise_seed + rank)",
+        "parallelism": f"replicas{world}" if world > 1 else "single",
     }
+
+
+def workload_intensities(w, rank: int = 0) -> np.ndarray:
+    """The default workload's data: the simulated measurement, Poisson-sampled on the host."""
+    d_clean = synth.measure_intensities(w.z_true, w.q_true, w.pos)
+    rng = np.random.Generator(np.random.PCG64(w.params["noise_seed"] + rank))
+    return synth.poisson_noise(d_clean, w.params["peak"], rng).astype(np.float32)
 
 
 def kernel_hash() -> str:
@@ -314,11 +325,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     w = synth.make_workload(WORKLOAD)
-    import oracle as O
-
-    d = O.forward_intensity(w.q_true, w.z_true, w.pos)
-    rng = np.random.Generator(np.random.PCG64(w.params["noise_seed"]))
-    d = synth.poisson_noise(d, w.params["peak"], rng).astype(np.float32)
+    d = workload_intensities(w, 0)
     per_step = []
     B = w.params["minibatch"]
     for i in range(args.warmup + args.steps):
@@ -332,7 +339,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(),
+        "data": "synthetic", "config": workload_config(world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"one minibatch of {B} positions per step from the initial state"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -354,7 +361,7 @@ def run_gpu(args, world, rank, local):
     w = synth.make_workload(WORKLOAD)
     p = w.params
     m, N, B = p["m"], len(w.pos), p["minibatch"]
-    d = host_intensities(w, rank)
+    d = workload_intensities(w, rank)
     params = emg.emg_default_params(alpha=p["alpha"], levels=p["levels"], minibatch=B,
                                     prolong=emg.EMG_PROLONG_BILINEAR if p["prolong"] == "bilinear"
                                     else emg.EMG_PROLONG_CONST, seed=p["order_seed"] + rank)
@@ -490,7 +497,7 @@ def run_gpu(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(workload_config(), parallelism=f"replicas{world}" if world > 1 else "single"),
+        "config": workload_config(world),
         "e2e": e2e, "gpu_launches": launches_total, "roofline": roofline, "clocks": clk,
         "misfit_end": phi_end,
         "scatter_atomic": {"value": world * N * args.steps / (atomic_ms / 1e3), "ms_per_step": atomic_ms / args.steps,

@@ -467,7 +467,10 @@ emg_status emg_profile_read(emg_ctx* ctx, double* ms, int64_t* launches);
  *  probe       device complex64 [m][m], updated in place
  *  pos         device int32 [n_pos][2] patch corners, |row|, |col| < 2^24
  *  intensity   device float32 [n_pos][m][m] data d_k in natural order (DC at [0][0])
- *  idx, b      host int32 [b] positions of this minibatch, 1 <= b <= n_pos
+ *  idx, b      host int32 [b] positions of this minibatch, 1 <= b <= n_pos,
+ *              b <= 2048; the indices are copied into the launch parameters
+ *              before the call returns, so the caller may reuse idx at once
+ *              (pinned or pageable)
  *  m           16, 32, 64 or 128 (EMG_ENOTSUP for 256)
  *  params      as for emg_create (minibatch and seed are ignored; dft must be
  *              EMG_DFT_FFT32, EMG_ENOTSUP for EMG_DFT_BF16X3)
@@ -483,7 +486,7 @@ emg_status emg_profile_read(emg_ctx* ctx, double* ms, int64_t* launches);
  * serialise them.  The first call on each device does a one-time set-up with
  * that device current (constant tables, kernel attributes, the scratch
  * address); make that first call before any stream capture.  Asynchronous on
- * `stream` otherwise (the host idx array is copied before the call returns).
+ * `stream` otherwise.
  */
 #define EMG_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
 emg_status emg_step_minibatch_noalloc(float* object, int32_t n_rows, int32_t n_cols,

@@ -29,9 +29,10 @@ follows the same readings):
   positions see the same snapshot (z, Q); covered object pixels become the
   weighted mean sum_k w_k z~_k / sum_k w_k with w_k = |Q(p - o_k)|^2 +
   eps max|Q|^2, and the probe becomes the plain mean of Q~_k over positions
-  whose patch is not identically zero.  B = 1 is the paper's update.  At
-  B > 1 the combine is parity unpinned: the paper fixes nothing it could be
-  checked against beyond B = 1 and non-overlapping patches, which are pinned.
+  whose patch is not identically zero.  B = 1 is the paper's update.  The
+  paper fixes nothing beyond B = 1, so B > 1 with overlapping patches is
+  pinned by a case worked by hand from these definitions (two overlapping
+  patches, an asymmetric probe, the weight floor active).
 * Geometric-mean branch: the principal root, negated when Re(root * conj(x))
   < 0; at exactly 0 the principal root is kept (Eq. geomean allows both).
 * A patch with max|z_k|^2 = 0 leaves the probe unchanged and is excluded from
@@ -345,9 +346,9 @@ def minibatch_step(z, Q, pos, a, idx, params: Params, out: Optional[dict] = None
     minibatch become sum_k w_k z~_k / sum_k w_k (``combine='wavg'``) or
     z + sum_k (z~_k - z_k) (``combine='sum'``); the probe becomes the mean of
     Q~_k (or Q + sum_k (Q~_k - Q)) over positions with mu_k > 0.
-    If ``out`` is a dict it receives per-position diagnostics.  Parity
-    unpinned at B > 1 with overlapping patches (the paper's sweep has batch 1);
-    B = 1 and non-overlapping minibatches are pinned against the sequential sweep.
+    If ``out`` is a dict it receives per-position diagnostics.  B = 1 and
+    non-overlapping minibatches are pinned against the paper's sequential
+    sweep; B > 1 with overlapping patches against a hand-worked case.
     """
     m = Q.shape[0]
     absQ2 = np.abs(Q) ** 2

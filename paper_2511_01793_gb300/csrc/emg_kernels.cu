@@ -2385,6 +2385,8 @@ cudaError_t launch_normalize_probe(const float* amp, int m, int n_pos, float2* p
 // scratch is the fixed array below, which every GPU that loads this library
 // holds until the process exits.
 // ===========================================================================
+#include <string.h>
+
 #include <mutex>
 
 #include "../../include/emagpie.h"
@@ -2460,6 +2462,18 @@ cudaError_t noalloc_setup(int dev, unsigned char** base) {
   return cudaSuccess;
 }
 
+// The minibatch's position indices travel inside the launch parameters, which
+// the runtime copies when the launch is enqueued: the caller may overwrite its
+// host array as soon as the call returns, pinned or not.
+constexpr int kNoAllocMaxIdx = 2048;
+struct NoAllocIdx {
+  int32_t v[kNoAllocMaxIdx];
+};
+
+__global__ void k_noalloc_idx(const NoAllocIdx p, int b, int32_t* __restrict__ out) {
+  for (int i = threadIdx.x; i < b; i += blockDim.x) out[i] = p.v[i];
+}
+
 template <int M>
 cudaError_t launch_step_natural(int b, const StepArgs& a, cudaStream_t s) {
   const size_t bytes = step_smem_elems<M>(a.levels) * sizeof(float2);
@@ -2477,7 +2491,7 @@ extern "C" emg_status emg_step_minibatch_noalloc(float* object, int32_t n_rows, 
                                                  const emg_params* p, emg_stream_t stream) {
   using namespace emg;
   if (!object || !probe || !pos || !intensity || !idx || !p) return EMG_EINVAL;
-  if (n_rows < 1 || n_cols < 1 || n_pos < 1 || b < 1 || b > n_pos) return EMG_EINVAL;
+  if (n_rows < 1 || n_cols < 1 || n_pos < 1 || b < 1 || b > n_pos || b > kNoAllocMaxIdx) return EMG_EINVAL;
   if (m != 16 && m != 32 && m != 64 && m != 128) return EMG_ENOTSUP;  // m = 256 needs a cluster
   if (!(p->alpha > 0.f) || !isfinite(p->alpha) || !(p->w_eps >= 0.f) || !isfinite(p->w_eps))
     return EMG_EINVAL;
@@ -2498,8 +2512,12 @@ extern "C" emg_status emg_step_minibatch_noalloc(float* object, int32_t n_rows, 
   if (cudaGetDevice(&dev) != cudaSuccess || noalloc_setup(dev, &base) != cudaSuccess) return EMG_ECUDA;
   const cudaStream_t s = (cudaStream_t)stream;
   int32_t* d_idx = (int32_t*)(base + L.idx);
-  if (cudaMemcpyAsync(d_idx, idx, (size_t)b * sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return EMG_ECUDA;
+  {
+    NoAllocIdx pv;
+    memcpy(pv.v, idx, (size_t)b * sizeof(int32_t));
+    k_noalloc_idx<<<1, 256, 0, s>>>(pv, b, d_idx);
+    if (cudaGetLastError() != cudaSuccess) return EMG_ECUDA;
+  }
 
   unsigned* d_mq = (unsigned*)(base + L.mq);
   if (cudaMemsetAsync(d_mq, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return EMG_ECUDA;

@@ -11,11 +11,11 @@
 // and can write them transposed per tile (the next pass then transforms the
 // other axis), replace the modulus (a3) or store FP32.
 //
-// Persistent kernel, one CTA per SM, in clusters of two CTAs that take the two
-// 128-row halves of a 256 x 256 output block: each CTA loads its own A rows and
-// half of the block's B (the DFT matrix) with a TMA multicast into both CTAs,
-// so B crosses L2 once per pair.  Warp 0 streams A and B chunks of 32 bf16
-// along K through a four-stage shared-memory ring with TMA (64-byte swizzle); warp 1 owns all 512 columns of tensor memory
+// Persistent kernel, one CTA per SM, each looping over 128 x 256 output tiles
+// (consecutive CTAs take the two 128-row halves of a 256-row block, so the
+// block's B, the DFT matrix, is read from L2 by both at about the same time).
+// Warp 0 streams A and B chunks of 32 bf16 along K through a four-stage
+// shared-memory ring with plain per-CTA TMA loads (64-byte swizzle); warp 1 owns all 512 columns of tensor memory
 // as two 256-column accumulators and issues tcgen05.mma from one lane; warps
 // 2-9 drain an accumulator with tcgen05.ld (two warps per lane quadrant, each
 // half of the columns) and run the epilogue while the MMAs of the next tile
@@ -108,23 +108,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// The same load with cluster multicast: the box lands at the same shared-memory
-// offset in every CTA of `mask` and completes bytes on the mbarrier at the same
-// offset in each of them.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -153,14 +136,6 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint6
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// Arrives (when the MMAs issued so far complete) on the mbarrier at this
-// offset in every CTA of `mask`.
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
-                   "r"(smem_u32(bar)), "h"(mask)
                : "memory");
 }
 
@@ -231,7 +206,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
              const TcPassArgs a) {
   extern __shared__ uint8_t tc_smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kStages];   // stage loaded (TMA bytes arrived)
-  __shared__ __align__(8) uint64_t empty_bar[kStages];  // stage consumed by the MMAs of both CTAs
+  __shared__ __align__(8) uint64_t empty_bar[kStages];  // stage consumed by the MMAs
   __shared__ __align__(8) uint64_t accf_bar[2];         // accumulator complete
   __shared__ __align__(8) uint64_t acce_bar[2];         // accumulator drained by the epilogue warps
   __shared__ __align__(8) uint64_t drain_bar;
@@ -247,7 +222,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 2);
+      mbar_init(&empty_bar[s], 1);
     }
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
@@ -256,7 +231,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     mbar_init(&drain_bar, 1);
     abort_sh = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");  // visible to the async proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
@@ -267,12 +242,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
-  cluster_sync_all();  // both CTAs' barriers exist before either multicasts into the other
+  __syncthreads();  // barriers initialised and the TMEM address published
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
+  // CTA pairs (2c, 2c + 1) take the two 128-row halves of the same output
+  // block, so both read that block's B rows from L2 at about the same time.
   const int rank = (int)(blockIdx.x & 1), n_cl = (int)(gridDim.x >> 1), cl_id = (int)(blockIdx.x >> 1);
   const int pairs = ((a.m_tiles + 1) >> 1) * a.tiles_n;
-  constexpr uint16_t kBoth = 3;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -290,11 +266,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           mbar_expect_tx(&full_bar[s], kStageBytes);
           tma_load_2d(st, &mAh, &full_bar[s], kc * kBK, m_tile * kBM);
           tma_load_2d(st + kTileA, &mAl, &full_bar[s], kc * kBK, m_tile * kBM);
-          // my half of the block's B rows, into both CTAs
-          const uint32_t bo = (uint32_t)rank * (kTileB / 2);
-          tma_load_2d_mc(st + 2 * kTileA + bo, &mBh, &full_bar[s], kc * kBK, n_tile * kBN + rank * (kBN / 2), kBoth);
-          tma_load_2d_mc(st + 2 * kTileA + kTileB + bo, &mBl, &full_bar[s], kc * kBK,
-                         n_tile * kBN + rank * (kBN / 2), kBoth);
+          // the block's B rows, in two boxes of kBN / 2 rows
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t bo = (uint32_t)h * (kTileB / 2);
+            tma_load_2d(st + 2 * kTileA + bo, &mBh, &full_bar[s], kc * kBK, n_tile * kBN + h * (kBN / 2));
+            tma_load_2d(st + 2 * kTileA + kTileB + bo, &mBl, &full_bar[s], kc * kBK, n_tile * kBN + h * (kBN / 2));
+          }
         }
       }
       if (abort_sh) {  // let the copies already issued land before the CTA exits
@@ -334,7 +312,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             umma_bf16(d, ah, bl, 1);
             umma_bf16(d, al, bh, 1);
           }
-          umma_commit_mc(&empty_bar[s], kBoth);  // the stage holds B rows that both CTAs load
+          umma_commit(&empty_bar[s]);  // the stage is free once these MMAs have read it
         }
         if (ok) umma_commit(&accf_bar[buf]);
       }
@@ -457,7 +435,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
-  cluster_sync_all();  // no CTA leaves while its partner may still multicast into it
 }
 
 // Complex64 tiles -> high / low bf16 pairs (same order).
@@ -648,21 +625,9 @@ cudaError_t launch_pass(const CUtensorMap& ah, const CUtensorMap& al, const CUte
   a.tiles_n = 2 * a.m / kBN;
   a.m_tiles = rows / kBM;
   const int pairs = ((a.m_tiles + 1) / 2) * a.tiles_n;
-  const int clusters = pairs < sms / 2 ? pairs : sms / 2;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2 * clusters);
-  cfg.blockDim = dim3(kTcThreads);
-  cfg.dynamicSmemBytes = kTcSmem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_dft<EPI>, ah, al, bh, bl, a);
-  return e != cudaSuccess ? e : cudaGetLastError();
+  const int npairs = pairs < sms / 2 ? pairs : sms / 2;
+  k_tc_dft<EPI><<<2 * npairs, kTcThreads, kTcSmem, s>>>(ah, al, bh, bl, a);
+  return cudaGetLastError();
 }
 
 cudaError_t set_tc_attrs() {

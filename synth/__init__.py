@@ -1,7 +1,9 @@
 """Seeded synthetic inputs for blind ptychography (object, probe, scan, noise).
 
 This module builds the *inputs* of a reconstruction and nothing of the method:
-no exit wave, no Fourier projection, no update rule.  Both the FP64 oracle
+no Fourier projection, no update rule.  Its one use of the FFT simulates the
+experiment (the far-field intensities of a known object and probe), so that
+two programs can be given identical data.  Both the FP64 oracle
 (tests) and the CUDA library (tests, bench) consume what it produces, so the
 two implementations always see identical arrays.
 
@@ -18,6 +20,7 @@ from .inputs import (  # noqa: F401
     make_scan,
     blur_probe,
     aberrate_probe,
+    measure_intensities,
     poisson_noise,
     noise_percent,
     epoch_orders,

@@ -152,6 +152,30 @@ def aberrate_probe(q: np.ndarray, rng: np.random.Generator, sigma: float = 2.0, 
     return q0 + scale * (rng.standard_normal(q.shape) + 1j * rng.standard_normal(q.shape))
 
 
+def measure_intensities(z_true: np.ndarray, q_true: np.ndarray, pos: np.ndarray,
+                        chunk: int = 64) -> np.ndarray:
+    """The simulated experiment: noise-free far-field intensities of a known
+    object and probe, |FFT2(Q * patch_k(z))|^2 per scan position (patches
+    zero-padded outside the object, DC at [0, 0]), float64 [N, m, m].
+
+    This is the measurement being simulated, not part of any reconstruction:
+    it produces the data that both implementations are then given.
+    """
+    m = q_true.shape[0]
+    n_rows, n_cols = z_true.shape
+    out = np.empty((len(pos), m, m), dtype=np.float64)
+    for c0 in range(0, len(pos), chunk):
+        block = np.zeros((min(chunk, len(pos) - c0), m, m), dtype=np.complex128)
+        for i, (r0, cc0) in enumerate(pos[c0:c0 + chunk]):
+            r0, cc0 = int(r0), int(cc0)
+            rs, re_ = max(r0, 0), min(r0 + m, n_rows)
+            cs, ce = max(cc0, 0), min(cc0 + m, n_cols)
+            if re_ > rs and ce > cs:
+                block[i, rs - r0:re_ - r0, cs - cc0:ce - cc0] = z_true[rs:re_, cs:ce]
+        out[c0:c0 + len(block)] = np.abs(np.fft.fft2(block * q_true[None])) ** 2
+    return out
+
+
 def poisson_noise(d_clean: np.ndarray, peak: float,
                   rng: np.random.Generator) -> np.ndarray:
     """Poisson counts at ``peak`` photons for the mean per-pattern maximum.
@@ -187,8 +211,8 @@ def perturb(x: np.ndarray, rel: float, rng: np.random.Generator) -> np.ndarray:
 def make_workload(name: str, n: Optional[int] = None, **override) -> Workload:
     """Object, probe, scan and blurred initial probe of a named configuration.
 
-    Intensities are *not* produced here: they are the forward model of the
-    method, computed by the oracle (tests) or the CUDA library (bench).
+    Intensities are not produced here: ``measure_intensities`` simulates them
+    on request (the tests use the oracle's forward model instead).
     """
     p = dict(CONFIGS[name])
     p.update(override)

@@ -357,6 +357,128 @@ def test_two_level_coarse_step_is_restricted_fine_step_for_blockwise_modulus():
     assert np.allclose(O.magpie_zplus(Q, z, R, u, 2, "const"), expect, atol=1e-13)
 
 
+def _fraction_blocks(name):
+    """[block] headers followed by rows of exact fractions (a hand-derived fixture)."""
+    from fractions import Fraction
+
+    blocks, cur = {}, None
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("["):
+                cur = line.strip("[]")
+                blocks[cur] = []
+            else:
+                blocks[cur].append([float(Fraction(t)) for t in line.split()])
+    return {k: np.array(v) for k, v in blocks.items()}
+
+
+def _bilinear_fixture_inputs():
+    Q = np.outer([2.0, 1.0, 1.0, 1.0], [1.0, 1.0, 1.0, 2.0]).astype(complex)
+    return Q, np.ones((4, 4), dtype=complex), 2 * Q, np.ones((4, 4))
+
+
+def test_two_level_bilinear_step_golden():
+    """Eq. def_weights and the two-level closed forms with bilinear prolongation, against the
+    hand-worked separable 4 x 4 case (a non-flat probe, so the coarse correction matters)."""
+    g = _fraction_blocks("magpie_bilinear_m4_l2.txt")
+    Q, z, R, u = _bilinear_fixture_inputs()
+    Wz, WR, WuH = O.mg_weights(Q, "bilinear")
+    assert np.max(np.abs(Wz - g["Wz"])) <= 1e-15
+    assert np.max(np.abs(WR - g["WR"])) <= 1e-15
+    assert np.max(np.abs(WuH - g["WuH"])) <= 1e-15
+    zp = O.magpie_zplus(Q, z, R, u, 2, "bilinear")
+    assert np.max(np.abs(zp - g["zplus"])) <= 1e-14
+    # the fine step does not erase the coarse correction here: z+ differs from R/Q
+    assert np.max(np.abs(zp - R / Q)) > 0.05
+
+
+def test_two_level_bilinear_golden_catches_constant_weights(monkeypatch):
+    """Planted mistake: piecewise-constant S inside the weights while the correction stays
+    bilinear.  The hand-worked fixture must reject it."""
+    g = _fraction_blocks("magpie_bilinear_m4_l2.txt")
+    Q, z, R, u = _bilinear_fixture_inputs()
+    import oracle.emagpie as OE
+
+    real = OE.mg_weights
+    monkeypatch.setattr(OE, "mg_weights", lambda Q_, kind="const": real(Q_, "const"))
+    zp = O.magpie_zplus(Q, z, R, u, 2, "bilinear")
+    assert np.max(np.abs(zp - g["zplus"])) > 1e-3
+
+
+def _overlap_fixture():
+    rows = {}
+    env = {"sqrt": math.sqrt, "__builtins__": {}}
+    with open(os.path.join(GOLDEN, "minibatch_overlap_m2.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            mode, what, *vals = [t.strip() for t in line.split("|")]
+            rows[(mode, what)] = np.array([eval(v, env) for v in vals])
+    z = np.full((2, 4), 0.6 + 0.8j)
+    Q = np.array([[2.0, 1.0], [3.0, 1.0]], dtype=complex)
+    pos = np.array([[0, 0], [0, 1]], dtype=np.int32)
+    a = np.array([[[14.0, 6.0], [2.0, 2.0]], [[21.0, 9.0], [3.0, 3.0]]])
+    return rows, z, Q, pos, a
+
+
+@pytest.mark.parametrize("mode", ["wavg", "sum"])
+def test_overlapping_minibatch_combine_golden(mode):
+    """The minibatch reading at B = 2 with overlapping patches and a non-flat probe, against
+    the hand-worked fixture: weights from the right probe pixel, the w_eps max|Q|^2 floor,
+    the shared snapshot, uncovered pixels untouched."""
+    rows, z, Q, pos, a = _overlap_fixture()
+    p = O.Params(alpha=0.5, levels=1, minibatch=2, combine=mode, w_eps=1.0 / 9.0)
+    z_new, Q_new = O.minibatch_step(z, Q, pos, a, [0, 1], p)
+    expect = np.stack([rows[(mode, "row0")], rows[(mode, "row1")]]) * z
+    assert np.max(np.abs(z_new - expect)) <= 1e-14
+    assert np.max(np.abs(Q_new - rows[(mode, "probe")][0] * Q)) <= 1e-14
+    # the order of the positions in the minibatch does not matter
+    z_rev, Q_rev = O.minibatch_step(z, Q, pos, a, [1, 0], p)
+    assert np.max(np.abs(z_rev - expect)) <= 1e-14
+
+
+def test_overlapping_minibatch_golden_catches_a_dropped_floor():
+    """Planted mistake: the weight floor w_eps max|Q|^2 left out.  Only the doubly covered
+    pixels move, and the fixture rejects them."""
+    rows, z, Q, pos, a = _overlap_fixture()
+    p = O.Params(alpha=0.5, levels=1, minibatch=2, combine="wavg", w_eps=0.0)
+    z_new, _ = O.minibatch_step(z, Q, pos, a, [0, 1], p)
+    expect = np.stack([rows[("wavg", "row0")], rows[("wavg", "row1")]]) * z
+    assert abs(z_new[0, 1] - expect[0, 1]) > 1e-3 and abs(z_new[1, 1] - expect[1, 1]) > 1e-3
+    others = np.ones((2, 4), dtype=bool)
+    others[:, 1] = False
+    assert np.max(np.abs(z_new[others] - expect[others])) <= 1e-14
+
+
+def test_overlapping_minibatch_golden_catches_a_transposed_weight():
+    """Planted mistake: the combine weight read from the transposed probe pixel, in a copy of
+    the oracle's source.  The asymmetric probe of the fixture makes the doubly covered pixels
+    move."""
+    import sys
+    import types
+
+    import oracle.emagpie as OE
+
+    src = open(OE.__file__).read()
+    right = 'num[obj] += w[pat] * st["z_t"][pat]\n        den[obj] += w[pat]'
+    wrong = 'num[obj] += w.T[pat] * st["z_t"][pat]\n        den[obj] += w.T[pat]'
+    assert src.count(right) == 1
+    mutant = types.ModuleType("oracle_mutant_wT")
+    sys.modules[mutant.__name__] = mutant
+    try:
+        exec(compile(src.replace(right, wrong), "oracle_mutant_wT", "exec"), mutant.__dict__)
+        rows, z, Q, pos, a = _overlap_fixture()
+        p = mutant.Params(alpha=0.5, levels=1, minibatch=2, combine="wavg", w_eps=1.0 / 9.0)
+        z_new, _ = mutant.minibatch_step(z, Q, pos, a, [0, 1], p)
+    finally:
+        del sys.modules[mutant.__name__]
+    expect = np.stack([rows[("wavg", "row0")], rows[("wavg", "row1")]]) * z
+    assert np.max(np.abs(z_new - expect)) > 1e-3
+
+
 # ------------------------------------------------- whole-step invariants
 
 def _tiny_workload(levels, m=16, n=40, side=4, step=6):
