@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-next-rows", action="store_true",
+                    help="default workload only: skip the short runs of the gradient, batch and precision "
+                         "workloads that ride along in the line")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "grad_n1024_m256", "batch64", "prec_n2048_m256"],
                     help="mg_n512_m128: eMAGPIE epochs (default); grad_n1024_m256: exit-wave "
@@ -250,6 +253,26 @@ def cpu_oracle_sample(w, d, seconds: float):
         b0 += B
         if time.perf_counter() - t0 >= seconds:
             break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def cpu_oracle_problem(sm, seconds: float):
+    """The FP64 oracle (as it stands) on consecutive minibatches of one batch problem."""
+    import oracle as O
+
+    a = np.sqrt(np.maximum(sm["d"].astype(np.float64), 0.0))
+    z = np.ones((sm["n"], sm["n"]), dtype=np.complex128)
+    q = sm["q0"].astype(np.complex128)
+    order = O.schedule_permutation(sm["seed"], 0, len(sm["pos"]))
+    prm = O.Params(alpha=0.05, levels=sm["levels"], minibatch=sm["B"], prolong="bilinear")
+    done, b0 = 0, 0
+    t0 = time.perf_counter()
+    while b0 < len(order) and time.perf_counter() - t0 < seconds:
+        idx = order[b0:b0 + sm["B"]]
+        z, q = O.minibatch_step(z, q, sm["pos"], a, idx, prm)
+        done += len(idx)
+        b0 += sm["B"]
     dt = time.perf_counter() - t0
     return done / dt, done, dt
 
@@ -516,8 +539,8 @@ def run_gpu(args, world, rank, local):
                 "value": rate_all, "unit": UNIT, "cores": procs,
                 "sample": f"{procs} independent oracle processes (spawned), each on the sample above; "
                           f"{done_all} positions in {dt_all:.1f} s"}
-    print(json.dumps(line), flush=True)
     ctx.close()
+    return line
 
 
 def run_gpu_grad(args, world, rank, local):
@@ -635,9 +658,8 @@ def run_gpu_grad(args, world, rank, local):
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"gradients of {done} positions, {dt:.1f} s single-thread FP64"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     ctx.close()
+    return line if rank == 0 else None
 
 
 PREC_WORKLOAD = "prec_n2048_m256"
@@ -787,14 +809,14 @@ def run_gpu_prec(args, world, rank, local):
     if rank != 0:
         for r in res.values():
             r["ctx"].close()
-        return
+        return None
     if world == 1 and not args.no_cpu_baseline:
         rate, done, dt = cpu_oracle_sample(w, d, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{done} positions from the initial state, {dt:.1f} s single-thread FP64"}
-    print(json.dumps(line), flush=True)
     for r in res.values():
         r["ctx"].close()
+    return line
 
 
 def batch_problems(count: int = 64, seed: int = 1003):
@@ -827,6 +849,7 @@ def run_gpu_batch(args, world, rank, local):
     probs = batch_problems()
     stream = torch.cuda.Stream()
     ctxs, total_pos, alg_bytes, tiles, batches = [], 0, 0, {}, {}
+    hosts, samples = [], []
     gen = torch.Generator(device="cuda")
     with torch.cuda.stream(stream):
         for pr in probs:
@@ -856,6 +879,11 @@ def run_gpu_batch(args, world, rank, local):
                                             trial_epochs=2, tune_tiling=True, allow_atomic=False)
             tiles[f"m{m}"] = tiles.get(f"m{m}", []) + [tuned["cluster"]]
             batches[f"m{m}"] = batches.get(f"m{m}", []) + [tuned["minibatch"]]
+            if not args.no_e2e:
+                hosts.append(d.cpu().pin_memory())
+            if not samples and rank == 0 and not args.no_cpu_baseline:
+                samples.append(dict(pos=pos, d=d.cpu().numpy(), n=n, q0=ctx.probe.cpu().numpy(), levels=pr["levels"],
+                                    B=tuned["minibatch"], seed=pr["seed"], m=m))
             del ctx.intensity
             ctxs.append(ctx)
             total_pos += N
@@ -877,6 +905,35 @@ def run_gpu_batch(args, world, rank, local):
         clk = clocks.stop()
         total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
         launches = sum(sum(v[1] for v in emg.emg_profile_read(c.ctx).values()) for c in ctxs)
+        e2e = None
+        if hosts:
+            # end to end through the public calls: every step uploads every problem's intensities
+            # (pinned host memory, read in place by the amplitude kernel) and its state, runs the
+            # batch epoch and reads every state back
+            z_in = [c.obj.cpu().pin_memory() for c in ctxs]
+            q_in = [c.probe.cpu().pin_memory() for c in ctxs]
+            z_out = [torch.empty_like(z).pin_memory() for z in z_in]
+            q_out = [torch.empty_like(q).pin_memory() for q in q_in]
+            t_e2e = 0.0
+            for i in range(args.steps + 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for c, dh, zh, qh in zip(ctxs, hosts, z_in, q_in):
+                    emg.emg_set_intensity(c.ctx, dh.data_ptr())
+                    c.obj.copy_(zh, non_blocking=True)
+                    c.probe.copy_(qh, non_blocking=True)
+                emg.emg_batch_run_epochs(batch, 1, stream.cuda_stream)
+                for c, zo, qo in zip(ctxs, z_out, q_out):
+                    zo.copy_(c.obj, non_blocking=True)
+                    qo.copy_(c.probe, non_blocking=True)
+                torch.cuda.synchronize()
+                if i > 0:      # the first round pays one-time costs
+                    t_e2e += time.perf_counter() - t0
+            t_e2e = max_over_ranks(t_e2e, world)
+            e2e = {"value": world * total_pos * args.steps / t_e2e, "unit": UNIT,
+                   "h2d_bytes_per_step": int(sum(h.nbytes for h in hosts) + sum(z.nbytes for z in z_in) +
+                                             sum(q.nbytes for q in q_in)),
+                   "d2h_bytes_per_step": int(sum(z.nbytes for z in z_out) + sum(q.nbytes for q in q_out))}
         emg.emg_batch_destroy(batch)
     value = world * total_pos * args.steps / (total_ms / 1e3)
     achieved = alg_bytes * args.steps / (total_ms / 1e3) / 1e9
@@ -892,16 +949,61 @@ def run_gpu_batch(args, world, rank, local):
                    "minibatch_chosen": {k: {str(b): v.count(b) for b in sorted(set(v))} for k, v in batches.items()},
                    "autotune": "per problem: B from {16, 32, 64} by misfit decrease per second over two trial "
                                "epochs, then the FFT tiling by epoch time; deterministic scatter"},
-        "e2e": None, "gpu_launches": launches,
+        "e2e": e2e, "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 5), "peak_source": peak_kind, "traffic": None,
                      "kernel": "whole epoch graph (algorithmic bytes of all positions / epoch time)"},
         "clocks": clk,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    if samples:
+        sm = samples[0]
+        rate, done, dt = cpu_oracle_problem(sm, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"problem 0 of the batch (object {sm['n']}^2, probe {sm['m']}^2, "
+                                          f"{len(sm['pos'])} positions, B = {sm['B']}): {done} positions from its "
+                                          f"initial state, {dt:.1f} s single-thread FP64"}
     for c in ctxs:
         c.close()
+    return line if rank == 0 else None
+
+
+def compact(line):
+    """The figures of a next-row workload that ride along in the default line."""
+    if line is None:
+        return None
+    keep = {k: line.get(k) for k in ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype", "clocks",
+                                     "gpu_launches")}
+    keep["workload"] = line["config"]["workload"]
+    rf = line.get("roofline") or {}
+    keep["roofline"] = {k: rf.get(k) for k in ("bound", "achieved", "peak", "unit", "frac", "kernel")}
+    if line.get("e2e"):
+        keep["e2e"] = line["e2e"]
+    if line.get("cpu_baseline"):
+        cb = line["cpu_baseline"]
+        keep["cpu_baseline"] = {k: cb.get(k) for k in ("value", "unit", "cores", "kind", "sample")}
+    for k in ("fft32", "time_to_oracle_misfit"):
+        if k in line:
+            keep[k] = line[k]
+    return keep
+
+
+def next_rows(args, world, rank, local):
+    """The three next-row workloads, each with a few timed steps, for the default line."""
+    sub = argparse.Namespace(**vars(args))
+    sub.steps, sub.warmup = min(args.steps, 5), max(3, min(args.warmup, 3))
+    sub.cpu_seconds = min(args.cpu_seconds, 6.0)
+    out = {}
+    for name, fn in (("grad_n1024_m256", run_gpu_grad), ("batch64", run_gpu_batch),
+                     (PREC_WORKLOAD, run_gpu_prec)):
+        sub.workload = name
+        t0 = time.perf_counter()
+        try:
+            out[name] = compact(fn(sub, world, rank, local))
+        except Exception as exc:  # a failed next row must not cost the main line
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"}
+        if out[name] is not None:
+            out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 def main():
@@ -910,16 +1012,15 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    if args.workload == "grad_n1024_m256":
-        run_gpu_grad(args, world, rank, local)
-        return
-    if args.workload == "batch64":
-        run_gpu_batch(args, world, rank, local)
-        return
-    if args.workload == PREC_WORKLOAD:
-        run_gpu_prec(args, world, rank, local)
-        return
-    run_gpu(args, world, rank, local)
+    fn = {"grad_n1024_m256": run_gpu_grad, "batch64": run_gpu_batch, PREC_WORKLOAD: run_gpu_prec}.get(args.workload)
+    if fn is not None:
+        line = fn(args, world, rank, local)
+    else:
+        line = run_gpu(args, world, rank, local)
+        if world == 1 and not args.no_next_rows:
+            line["next_rows"] = next_rows(args, world, rank, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -291,6 +291,72 @@ emg_status emg_simulate_intensity(const float* object, int32_t n_rows, int32_t n
                                   int32_t n_pos, float* out, emg_stream_t stream);
 
 /*
+ * One minibatch split across ranks (one process per GPU, each with its own
+ * context on identical state and data).  The minibatch's slots 0..b-1 (slot k
+ * holds position idx[k]) are divided among the ranks; each rank steps its own
+ * slots against the shared snapshot (z, Q), the ranks exchange the results
+ * (one all-gather of the slot buffers), and every rank then combines all b
+ * slots in slot order, so all ranks end with bitwise the same state, equal to
+ * emg_step_minibatch on one GPU.  The paper's sweep has batch 1 (Sec. 4.4);
+ * this is the minibatch reading of the sweep with its positions spread over
+ * devices.
+ *
+ * emg_shard_step: probe prep and the per-position step (a0-a7) for slots
+ *   [slot_begin, slot_end); writes z~_k to zt + k m^2, Q~_k to qt + k m^2
+ *   (complex64) and max|z_k|^2 to mu + k for each of those slots.  The bound
+ *   object and probe are not changed.  slot_begin == slot_end is allowed (the
+ *   rank has no position in this minibatch).
+ * emg_shard_apply: the combine (a8, a9) of all b slots read from zt, qt, mu,
+ *   which by then hold every rank's slots; updates the bound object and probe.
+ *  idx, b   host int32 [b], the whole minibatch, the same on every rank
+ *  zt, qt   device complex64 [>= b][m][m], caller-owned
+ *  mu       device float32 [>= b], caller-owned
+ * EMG_ENOTSUP with the atomic scatter (it has no per-slot patches to
+ * exchange).  Asynchronous on the context's stream; the caller orders its
+ * exchange on that stream between the two calls.
+ */
+emg_status emg_shard_step(emg_ctx* ctx, const int32_t* idx, int32_t b, int32_t slot_begin,
+                          int32_t slot_end, float* zt, float* qt, float* mu);
+emg_status emg_shard_apply(emg_ctx* ctx, const int32_t* idx, int32_t b, const float* zt,
+                           const float* qt, const float* mu);
+
+/*
+ * Reconstruction errors with the scale ambiguity removed, reduced on the GPU
+ * in FP64.  Blind ptychography determines (z, Q) only up to (c z, Q / c) for a
+ * complex c != 0: the exit waves Q . P_k z of Sec. 2.1, and so the data, do
+ * not change.  The call takes the best c over a region of the object,
+ *   c = <z, z_ref> / <z, z>     (<a, b> = sum over the region of conj(a) b),
+ * and returns in out (host double[5]):
+ *   out[0], out[1]  Re c, Im c
+ *   out[2]          ||c z - z_ref|| / ||z_ref|| over the region
+ *   out[3]          ||Q / c - Q_ref|| / ||Q_ref|| over the whole probe
+ *   out[4]          RMS over the region of arg(c z conj(z_ref)) (radians)
+ *  object, object_ref  device complex64 [n_rows][n_cols]
+ *  probe, probe_ref    device complex64 [m][m]
+ *  region              device uint8 [n_rows][n_cols], nonzero = inside; NULL = every pixel
+ * Sums run in a fixed order, so the result is bitwise repeatable.  Allocates
+ * a small scratch buffer (EMG_ENOMEM if that fails) and synchronises `stream`.
+ */
+emg_status emg_aligned_errors(const float* object, const float* object_ref, int32_t n_rows,
+                              int32_t n_cols, const float* probe, const float* probe_ref, int32_t m,
+                              const uint8_t* region, double* out, emg_stream_t stream);
+
+/*
+ * The well-illuminated region of the scan, the comparison region of
+ * emg_aligned_errors: region[p] = 1 where sum_k |probe_ref(p - o_k)|^2 >=
+ * frac * (its maximum over the object), else 0 (o_k = pos[k], the patch
+ * corners of Sec. 2.1; pixels a patch does not cover add nothing).  The sums
+ * are FP64 over k = 0..n_pos-1 in index order.
+ *  probe_ref  device complex64 [m][m]
+ *  pos        device int32 [n_pos][2]
+ *  region     device uint8 [n_rows][n_cols], written
+ * Allocates n_rows n_cols doubles of scratch and synchronises `stream`.
+ */
+emg_status emg_illuminated_region(const float* probe_ref, int32_t m, const int32_t* pos,
+                                  int32_t n_pos, int32_t n_rows, int32_t n_cols, double frac,
+                                  uint8_t* region, emg_stream_t stream);
+
+/*
  * Batched 2-D DFT of count m x m complex64 tiles (device, natural order in
  * and out): inverse = 0 gives F x (unnormalised), inverse = 1 gives F^-1 x
  * (with 1/m^2).  in and out may alias.  Asynchronous on `stream`.

@@ -26,7 +26,9 @@ __all__ = [
     "emg_create", "emg_set_intensity", "emg_bind_state", "emg_normalize_probe",
     "emg_step_minibatch", "emg_position_stats", "emg_set_verify", "emg_run_epochs", "emg_misfit",
     "emg_set_epoch", "emg_schedule_permutation", "emg_stopping_epoch", "emg_run_until", "emg_reconstruct_host",
-    "emg_simulate_intensity", "emg_fft2", "emg_dft2_bf16x3", "emg_step_minibatch_noalloc", "emg_misfit_gradient",
+    "emg_simulate_intensity", "emg_fft2", "emg_dft2_bf16x3", "emg_aligned_errors", "emg_shard_step",
+    "emg_shard_apply",
+    "emg_illuminated_region", "emg_step_minibatch_noalloc", "emg_misfit_gradient",
     "emg_set_cluster", "emg_set_prep_fusion", "emg_debug_prep_wait_extra", "emg_set_gradient_chunk", "emg_autotune", "emg_set_minibatch", "emg_set_scatter",
     "emg_selftest_bounded_wait", "emg_debug_fail_alloc", "emg_debug_bounds_errors",
     "emg_debug_bounds_selftest",
@@ -98,6 +100,12 @@ _SIGS = {
     "emg_simulate_intensity": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_int32,
                                               _VP, ctypes.c_int32, _VP, _VP]),
     "emg_fft2": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP]),
+    "emg_shard_step": (ctypes.c_int, [_VP, _I32P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
+    "emg_shard_apply": (ctypes.c_int, [_VP, _I32P, ctypes.c_int32, _VP, _VP, _VP]),
+    "emg_aligned_errors": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, ctypes.c_int32,
+                                          _VP, _F64P, _VP]),
+    "emg_illuminated_region": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_double, _VP, _VP]),
     "emg_stopping_epoch": (ctypes.c_int, [_F64P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_int32)]),
     "emg_run_until": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
@@ -310,6 +318,36 @@ def emg_run_until(ctx: int, max_epochs: int, window: int = 5, patience: int = 10
 
 def emg_fft2(in_ptr: int, out_ptr: int, m: int, count: int, inverse: bool, stream: int = 0) -> None:
     _check(load().emg_fft2(in_ptr, out_ptr, m, count, int(bool(inverse)), _VP(stream)), "emg_fft2")
+
+
+def emg_shard_step(ctx: int, idx, slot_begin: int, slot_end: int, zt_ptr: int, qt_ptr: int, mu_ptr: int) -> None:
+    """The per-position step for slots [slot_begin, slot_end) of minibatch idx into caller buffers."""
+    a = _i32(idx)
+    _check(load().emg_shard_step(ctx, _ptr_i32(a), len(a), slot_begin, slot_end, zt_ptr, qt_ptr, mu_ptr),
+           "emg_shard_step", ctx)
+
+
+def emg_shard_apply(ctx: int, idx, zt_ptr: int, qt_ptr: int, mu_ptr: int) -> None:
+    """The combine of all slots of minibatch idx from caller buffers (after the exchange)."""
+    a = _i32(idx)
+    _check(load().emg_shard_apply(ctx, _ptr_i32(a), len(a), zt_ptr, qt_ptr, mu_ptr), "emg_shard_apply", ctx)
+
+
+def emg_aligned_errors(object_ptr: int, object_ref_ptr: int, n_rows: int, n_cols: int, probe_ptr: int,
+                       probe_ref_ptr: int, m: int, region_ptr: int = 0, stream: int = 0) -> dict:
+    """FP64 errors after the best scale c (z -> c z, Q -> Q / c); see include/emagpie.h."""
+    out = np.zeros(5, dtype=np.float64)
+    _check(load().emg_aligned_errors(object_ptr, object_ref_ptr, n_rows, n_cols, probe_ptr, probe_ref_ptr, m,
+                                     region_ptr or None, out.ctypes.data_as(_F64P), _VP(stream)),
+           "emg_aligned_errors")
+    return dict(c=complex(out[0], out[1]), object=float(out[2]), probe=float(out[3]), phase_rms=float(out[4]))
+
+
+def emg_illuminated_region(probe_ref_ptr: int, m: int, pos_ptr: int, n_pos: int, n_rows: int, n_cols: int,
+                           frac: float, region_ptr: int, stream: int = 0) -> None:
+    """Writes the uint8 mask of pixels with summed illumination >= frac * max."""
+    _check(load().emg_illuminated_region(probe_ref_ptr, m, pos_ptr, n_pos, n_rows, n_cols, float(frac),
+                                         region_ptr, _VP(stream)), "emg_illuminated_region")
 
 
 def emg_dft2_bf16x3(in_ptr: int, out_ptr: int, m: int, count: int, inverse: bool, stream: int = 0) -> None:

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB_NAME = "libemagpie.so"
-SOURCES = ["emg_kernels.cu", "emg_capi.cu", "emg_tc.cu"]
+SOURCES = ["emg_kernels.cu", "emg_capi.cu", "emg_tc.cu", "emg_metrics.cu"]
 HEADERS = ["emg_fft.cuh", "emg_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ftz=true: FP32 denormals flush to zero (the data never come near 1e-38).

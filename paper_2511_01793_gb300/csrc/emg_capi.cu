@@ -424,12 +424,32 @@ emg_status seed_probe_max(emg_ctx* c, cudaStream_t s) {
   return EMG_OK;
 }
 
+// One rank's part of a minibatch split across ranks: the step covers slots
+// [s0, s1) and writes z~_k, Q~_k, mu_k of slot k to zt + k m^2, qt + k m^2,
+// mu + k (caller-owned buffers of all slots); with `step` false the step is
+// skipped and the combine reads every slot from those buffers.
+struct ShardPart {
+  int s0, s1;
+  float2* zt;
+  float2* qt;
+  float* mu;
+  bool step, apply;
+};
+
 // Enqueues one minibatch: probe prep, per-position step, combine.  `seq` is the
 // minibatch's index within the current call: it selects which max|Q|^2 slot
 // the prep reads and which one the combine fills.
 emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_phi_out, int seq,
-                             cudaStream_t strm) {
+                             cudaStream_t strm, const ShardPart* sh = nullptr) {
   if (!c->object || !c->probe) return fail(c, EMG_EINVAL, "no state bound");
+  const size_t mm = (size_t)c->m * c->m;
+  // the slots this call steps (all of them unless a shard says otherwise)
+  const int s0 = sh ? sh->s0 : 0, nb = sh ? sh->s1 - sh->s0 : b;
+  const bool do_step = !sh || sh->step, do_apply = !sh || sh->apply;
+  float2* zt_all = sh ? sh->zt : c->d_zt;
+  float2* qt_all = sh ? sh->qt : c->d_qt;
+  float* mu_all = sh ? sh->mu : c->d_mu;
+  if (do_step) {
   PrepArgs pa = c->prep;
   pa.probe = c->probe;  // the probe bound right now (emg_reconstruct_host swaps it)
   pa.mq_read = c->d_mq + (seq & 1);
@@ -438,7 +458,7 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   if (c->stream_src) {  // this minibatch's amplitudes, read from host memory on the side stream
     {
       LaunchMark mk(c, kKindOther);
-      e = emg::launch_amp_gather(c->stream_src, d_idx, b, c->d_amp, c->m, c->side);
+      e = emg::launch_amp_gather(c->stream_src, d_idx + s0, nb, c->d_amp, c->m, c->side);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "k_amp_gather launch");
     EMG_CUDA(c, cudaEventRecord(c->ev_side, c->side));
@@ -454,7 +474,7 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
       c->resident_clusters = emg::step_resident_clusters(c->m, c->cluster);
       c->resident_cluster = c->cluster;
     }
-    if (b + prep_clusters > c->resident_clusters) fused_tiles = 0;
+    if (nb + prep_clusters > c->resident_clusters || nb == 0) fused_tiles = 0;
   }
   if (fused_tiles == 0) {
     {
@@ -469,11 +489,11 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   sa.probe = c->probe;
   sa.pos = c->d_pos;
   sa.amp = c->d_amp;
-  sa.order = d_idx;
+  sa.order = d_idx + s0;
   sa.mq = pa.mq_read;
   sa.n_rows = c->n_rows;
   sa.n_pos = c->n_pos;
-  sa.b = b;
+  sa.b = nb;
   sa.n_cols = c->n_cols;
   sa.levels = c->par.levels;
   sa.prolong = c->par.prolong;
@@ -482,10 +502,10 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   sa.cluster = c->cluster;
   sa.alpha = c->par.alpha;
   sa.lv = c->lv;
-  sa.zt = c->d_zt;
-  sa.qt = c->d_qt;
-  sa.mu = c->d_mu;
-  sa.phi = d_phi_out;
+  sa.zt = zt_all + (size_t)s0 * mm;
+  sa.qt = qt_all + (size_t)s0 * mm;
+  sa.mu = mu_all + s0;
+  sa.phi = d_phi_out + s0;
   sa.phi_after = c->d_phi_after;
   sa.combine = c->par.combine;
   sa.w_eps = c->par.w_eps;
@@ -499,18 +519,20 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
     sa.prep_clusters = (fused_tiles + c->cluster - 1) / c->cluster;
     sa.ticket_base = c->ticket_base;
     sa.prep_target = c->prep_done_base + (unsigned)fused_tiles + c->prep_wait_extra;
-    c->ticket_base += (unsigned)(b + sa.prep_clusters);
+    c->ticket_base += (unsigned)(nb + sa.prep_clusters);
     c->prep_done_base += (unsigned)fused_tiles;
   }
-  if (c->tc) {
+  if (nb == 0) {
+    // an empty share: only the prep ran (the combine needs its weights)
+  } else if (c->tc) {
     emg::TcStepArgs ta{};
     ta.object = c->object;
     ta.probe = c->probe;
     ta.pos = c->d_pos;
-    ta.order = d_idx;
+    ta.order = d_idx + s0;
     ta.n_rows = c->n_rows;
     ta.n_cols = c->n_cols;
-    ta.b = b;
+    ta.b = nb;
     ta.amp_t = c->d_amp_t;
     ta.R = c->d_tc_r;
     ta.partial = c->d_tc_part;
@@ -524,13 +546,17 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
     sa.r_tiles = emg::tc_tiles_per_position(c->m);
     {
       LaunchMark mk(c, kKindStep);
-      e = emg::launch_step_rin(c->m, b, sa, strm);
+      e = emg::launch_step_rin(c->m, nb, sa, strm);
     }
   } else {
     LaunchMark mk(c, kKindStep);
-    e = emg::launch_step(c->m, b, sa, strm);
+    e = emg::launch_step(c->m, nb, sa, strm);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_step launch");
+  }  // do_step
+  if (!do_apply) return EMG_OK;
+  const bool atomic = c->par.scatter == EMG_SCATTER_ATOMIC;
+  cudaError_t e;
   ApplyArgs aa{};
   aa.object = c->object;
   aa.probe = c->probe;
@@ -542,9 +568,9 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   aa.n_cols = c->n_cols;
   aa.m = c->m;
   aa.combine = c->par.combine;
-  aa.zt = c->d_zt;
-  aa.qt = c->d_qt;
-  aa.mu = c->d_mu;
+  aa.zt = zt_all;
+  aa.qt = qt_all;
+  aa.mu = mu_all;
   aa.wq = c->d_wq;
   aa.mq_next = c->d_mq + ((seq + 1) & 1);
   aa.tiles_x = (c->n_cols + emg::kApplyTile - 1) / emg::kApplyTile;
@@ -1060,6 +1086,49 @@ emg_status emg_step_minibatch(emg_ctx* c, const int32_t* idx, int32_t b, double*
     *sampled_misfit = c->h_scalar[0];
     return check_tc_flag(c);
   }
+  return EMG_OK;
+}
+
+// Checks shared by the two halves of a minibatch split across ranks.
+emg_status shard_args(emg_ctx* c, const int32_t* idx, int32_t b, const void* zt, const void* qt, const void* mu) {
+  if (!c) return EMG_EINVAL;
+  emg_status st = check_bound(c);
+  if (st != EMG_OK) return st;
+  if (!idx || !zt || !qt || !mu) return fail(c, EMG_EINVAL, "idx, zt, qt and mu must not be NULL");
+  if (b < 1 || b > c->par.minibatch) return fail(c, EMG_EINVAL, "b must be in [1, params.minibatch]");
+  if (c->par.scatter == EMG_SCATTER_ATOMIC)
+    return fail(c, EMG_ENOTSUP, "a split minibatch exchanges patches; the atomic scatter has none");
+  for (int i = 0; i < b; ++i)
+    if (idx[i] < 0 || idx[i] >= c->n_pos) return fail(c, EMG_EINVAL, "idx entry out of range");
+  return EMG_OK;
+}
+
+emg_status emg_shard_step(emg_ctx* c, const int32_t* idx, int32_t b, int32_t slot_begin, int32_t slot_end,
+                          float* zt, float* qt, float* mu) {
+  NvtxRange nvtx_range("emg_shard_step");
+  emg_status st = shard_args(c, idx, b, zt, qt, mu);
+  if (st != EMG_OK) return st;
+  if (slot_begin < 0 || slot_end < slot_begin || slot_end > b)
+    return fail(c, EMG_EINVAL, "need 0 <= slot_begin <= slot_end <= b");
+  DeviceGuard g(c->device);
+  if ((st = ensure_orders(c, (size_t)c->n_pos)) != EMG_OK) return st;
+  if ((st = upload_orders(c, idx, (size_t)b, c->stream)) != EMG_OK) return st;
+  if ((st = seed_probe_max(c, c->stream)) != EMG_OK) return st;
+  ShardPart sh{slot_begin, slot_end, (float2*)zt, (float2*)qt, mu, true, false};
+  return enqueue_minibatch(c, c->d_orders, b, c->d_phi, 0, c->stream, &sh);
+}
+
+emg_status emg_shard_apply(emg_ctx* c, const int32_t* idx, int32_t b, const float* zt, const float* qt,
+                           const float* mu) {
+  NvtxRange nvtx_range("emg_shard_apply");
+  emg_status st = shard_args(c, idx, b, zt, qt, mu);
+  if (st != EMG_OK) return st;
+  DeviceGuard g(c->device);
+  if ((st = ensure_orders(c, (size_t)c->n_pos)) != EMG_OK) return st;
+  if ((st = upload_orders(c, idx, (size_t)b, c->stream)) != EMG_OK) return st;
+  ShardPart sh{0, 0, (float2*)zt, (float2*)qt, (float*)mu, false, true};
+  if ((st = enqueue_minibatch(c, c->d_orders, b, c->d_phi, 0, c->stream, &sh)) != EMG_OK) return st;
+  c->last_b = b;
   return EMG_OK;
 }
 

@@ -105,3 +105,62 @@ def covered_mask(case: Case, idx):
 
 def log_rel(a, b):
     return math.log10(max(rel_err(a, b), 1e-30))
+
+
+def jiggle(x, seed):
+    """x perturbed by about one FP32 rounding (2^-24 relative), seeded."""
+    rng = np.random.default_rng(1000 + seed)
+    return x * (1 + 2.0 ** -24 * (rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape)))
+
+
+def oracle_epoch_states(args):
+    """FP64 oracle epochs from (z0, q0), optionally jiggled: per epoch the
+    end-of-epoch misfit, the running misfit and the state (z, Q).  Runs in a
+    spawned worker process."""
+    z0, q0, pos, a, orders, p, member = args
+    if member is not None:
+        z0, q0 = jiggle(z0, member), jiggle(q0, 500 + member)
+    z, q = z0, q0
+    out = []
+    for order in orders:
+        z, q, hist = O.run_epochs(z, q, pos, a, order[None, :], p)
+        out.append((hist[0]["misfit"], hist[0]["running_misfit"], z.astype(np.complex128), q.astype(np.complex128)))
+    return out
+
+
+def oracle_ensemble_states(z0, q0, pos, a, orders, p, members):
+    """The central oracle run and `members` runs from jiggled inputs, in
+    parallel spawned processes (the oracle is single-threaded)."""
+    import multiprocessing as mp
+    import os
+
+    jobs = [(z0, q0, pos, a, orders, p, None)] + [(z0, q0, pos, a, orders, p, s) for s in range(members)]
+    procs = min(len(jobs), max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else 1))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(oracle_epoch_states, jobs)
+    return res[0], res[1:]
+
+
+def epoch_deviations(gpu, central, members, region):
+    """Per epoch: the GPU's deviation from the central oracle run, and the
+    envelope of the oracle ensemble: the largest deviation between any two of
+    its runs (the central one and the jiggled members), as a running maximum
+    over epochs.  The GPU passes when it is no farther from the oracle than the
+    oracle's own rounding-level runs are from one another.  Quantities: the
+    end-of-epoch misfit and the running misfit (relative), and the aligned
+    object, probe and RMS phase errors.  Each run is a list of (Phi, running, z, Q)."""
+    keys = ("misfit", "running", "object", "probe", "phase")
+
+    def dev(run, ref):
+        rows = []
+        for (mg, rg, zg, qg), (mo, ro, zo, qo) in zip(run, ref):
+            e = O.aligned_errors(zg, qg, zo, qo, region)
+            rows.append([abs(mg - mo) / mo, abs(rg - ro) / ro, e["object"], e["probe"], e["phase_rms"]])
+        return np.array(rows)
+
+    d_gpu = dev(gpu, central)
+    runs = [central] + list(members)
+    env = np.max(np.stack([dev(runs[i], runs[j]) for i in range(len(runs)) for j in range(len(runs)) if i != j]),
+                 axis=0)
+    env = np.maximum.accumulate(env, axis=0)
+    return keys, d_gpu, env
