@@ -53,6 +53,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--shard", action="store_true",
+                    help="default workload as ONE reconstruction whose minibatches are split across the "
+                         "ranks (one all-gather of the slot results per minibatch; strong scaling) instead "
+                         "of independent replicas")
     ap.add_argument("--no-next-rows", action="store_true",
                     help="default workload only: skip the short runs of the gradient, batch and precision "
                          "workloads that ride along in the line")
@@ -967,6 +971,71 @@ def run_gpu_batch(args, world, rank, local):
     return line if rank == 0 else None
 
 
+def run_gpu_shard(args, world, rank, local):
+    """One reconstruction of the default workload with every minibatch split across the ranks."""
+    import torch
+
+    import paper_2511_01793_gb300 as emg
+    from paper_2511_01793_gb300.shard import ShardedReconstruction
+
+    torch.cuda.set_device(local)
+    init_replicas(world, local)
+    emg.build()
+    emg.load()
+    w = synth.make_workload(WORKLOAD)
+    p = w.params
+    m, N, B = p["m"], len(w.pos), p["minibatch"]
+    d = workload_intensities(w, 0)            # the same data on every rank
+    params = emg.emg_default_params(alpha=p["alpha"], levels=p["levels"], minibatch=B,
+                                    prolong=emg.EMG_PROLONG_BILINEAR, seed=p["order_seed"])
+    stream = torch.cuda.Stream()
+    orders = synth.epoch_orders(N, args.warmup + args.steps, p["order_seed"])
+    with torch.cuda.stream(stream):
+        ctx = emg.Context(w.pos, d, p["n"], p["n"], params, obj=torch.ones((p["n"], p["n"]), dtype=torch.complex64),
+                          probe=torch.from_numpy(w.q_init_blurred.astype(np.complex64)), stream=stream)
+        emg.emg_normalize_probe(ctx.ctx)
+        emg.emg_set_cluster(ctx.ctx, CLUSTER)
+        run = ShardedReconstruction(ctx, world, rank)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+        def barrier():
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+        for e in range(args.warmup):
+            run.run_epoch(orders[e])
+        emg.emg_profile_read(ctx.ctx)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        clocks.start()
+        barrier()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            run.run_epoch(orders[args.warmup + i])
+            ev[i][1].record(stream)
+        barrier()
+        clk = clocks.stop()
+        total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
+        launches = sum(v[1] for v in emg.emg_profile_read(ctx.ctx).values())
+        phi_end = emg.emg_misfit(ctx.ctx)
+    ctx.close()
+    if rank != 0:
+        return None
+    value = N * args.steps / (total_ms / 1e3)       # one reconstruction: the job's positions per second
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(1), parallelism=f"minibatch split over {world} ranks"),
+        "e2e": None, "gpu_launches": launches, "roofline": None, "clocks": clk, "misfit_end": phi_end,
+        "note": "each minibatch: the ranks step their shares of the slots, one all-gather of the slot results, "
+                "the combine on every rank; minibatches run from Python without graph capture",
+    }
+
+
 def compact(line):
     """The figures of a next-row workload that ride along in the default line."""
     if line is None:
@@ -1013,6 +1082,8 @@ def main():
         run_reference(args, world, rank)
         return
     fn = {"grad_n1024_m256": run_gpu_grad, "batch64": run_gpu_batch, PREC_WORKLOAD: run_gpu_prec}.get(args.workload)
+    if args.shard and args.workload == WORKLOAD:
+        fn = run_gpu_shard
     if fn is not None:
         line = fn(args, world, rank, local)
     else:
