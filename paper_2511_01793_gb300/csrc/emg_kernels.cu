@@ -786,6 +786,7 @@ namespace cg = cooperative_groups;
 #define EMG_UPDATE_GROUP 8
 #endif
 
+
 // Cluster barrier arrive without release semantics, for barriers that order
 // execution only (every CTA of the cluster resident; no CTA exits while a
 // neighbour still reads its shared memory).  A release arrive would first
@@ -927,7 +928,14 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
 
   // a1: gather my rows, psi = Q z_k, partial mu_k
   float mu_l = 0.f;
-#pragma unroll 4
+  // pixels of a thread whose gather loads are in flight together (more costs
+  // registers that the small tiles need for their occupancy)
+#ifdef EMG_GATHER_UNROLL
+  constexpr int kGatherUnroll = EMG_GATHER_UNROLL;
+#else
+  constexpr int kGatherUnroll = M >= 128 ? 8 : 4;
+#endif
+#pragma unroll (kGatherUnroll)
   for (int t = 0; t < PER; ++t) {
     const int p = tid + t * NT;
     const int lr = p / M, c = p % M, r = row0 + lr;
@@ -1043,7 +1051,40 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
     }
   };
   const bool halo = a.prolong != 0;
+  // With three levels (and slabs that split evenly over the threads) every
+  // level array the coarse levels need is loaded into registers here, beside
+  // the loads of the first restriction, so the coarse phases wait on no load.
+  constexpr int wc1 = M / 2, hc1 = wc1 / C, wc2 = M / 4, hc2 = wc2 / C;
+  constexpr bool kL3 = hc2 >= 1 && hc2 * wc2 >= NT && (hc2 * wc2) % NT == 0 && (hc1 * wc1) % NT == 0;
+  constexpr int Q12 = kL3 ? hc2 * wc2 / NT : 1, QUP = kL3 ? hc1 * wc1 / NT : 1;
+  const bool l3 = kL3 && a.levels == 3;
+  float2 pf_wz1[Q12][2];     // W_z,1 at (2i + dy, 2j .. 2j + 1): (dx 0, dx 1) per dy
+  float4 pf_wr1[Q12][2];     // W_R,1 at the same pixels
+  float2 pf_g2[Q12], pf_q2[Q12], pf_g1[QUP], pf_q1[QUP];
   if (a.levels > 1) {
+    if (l3) {
+#pragma unroll
+      for (int t = 0; t < Q12; ++t) {
+        const int p = tid + t * NT, i = p / wc2, j = p % wc2;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const int r = rank * hc1 + 2 * i + dy, c = 2 * j;
+          const int wi = EMG_INB(r * wc1 + c + 1, wc1 * wc1, kBcLevel) ? r * wc1 + c : 0;
+          pf_wz1[t][dy] = __ldcg(reinterpret_cast<const float2*>(a.lv.Wz[1] + wi));
+          pf_wr1[t][dy] = __ldcg(reinterpret_cast<const float4*>(a.lv.WR[1] + wi));
+        }
+        const int li = EMG_INB((rank * hc2 + i) * wc2 + j, wc2 * wc2, kBcLevel) ? (rank * hc2 + i) * wc2 + j : 0;
+        pf_g2[t] = __ldcg(a.lv.G[2] + li);
+        pf_q2[t] = __ldcg(a.lv.Q[2] + li);
+      }
+#pragma unroll
+      for (int t = 0; t < QUP; ++t) {
+        const int p = tid + t * NT, i = p / wc1, j = p % wc1;
+        const int li = EMG_INB((rank * hc1 + i) * wc1 + j, wc1 * wc1, kBcLevel) ? (rank * hc1 + i) * wc1 + j : 0;
+        pf_g1[t] = __ldcg(a.lv.G[1] + li);
+        pf_q1[t] = __ldcg(a.lv.Q[1] + li);
+      }
+    }
     {  // restrict level 0 -> 1: z_1 = I_h^H (W_z z_k), R_1 = I_h^H (W_R R)
       constexpr int wc = M / 2, hc = wc / C, sc = wc + 1;
       constexpr int PC = hc * wc / NT;
@@ -1058,19 +1099,75 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
         const int i = p / wc, j = p % wc;
         float2 zs = czero(), rs = czero();
 #pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-          for (int dx = 0; dx < 2; ++dx) {
-            const int lr = 2 * i + dy, r = row0 + lr, c = 2 * j + dx;
-            const float2 zk = zbuf[lr * M + c];
-            zs = cadd(zs, cscale(zk, __ldcg(Wz + r * M + c)));
-            rs = cadd(rs, cmul(__ldcg(WR + r * M + c), rowbuf[lr * SR + c]));
-          }
+        for (int dy = 0; dy < 2; ++dy) {
+          const int lr = 2 * i + dy, r = row0 + lr, c = 2 * j;
+          // the weights of the pixel pair (c, c + 1) in one load each (c is even)
+          const float2 wz = __ldcg(reinterpret_cast<const float2*>(Wz + r * M + c));
+          const float4 wr = __ldcg(reinterpret_cast<const float4*>(WR + r * M + c));
+          zs = cadd(zs, cscale(zbuf[lr * M + c], wz.x));
+          rs = cadd(rs, cmul(make_float2(wr.x, wr.y), rowbuf[lr * SR + c]));
+          zs = cadd(zs, cscale(zbuf[lr * M + c + 1], wz.y));
+          rs = cadd(rs, cmul(make_float2(wr.z, wr.w), rowbuf[lr * SR + c + 1]));
+        }
         Z1w[i * sc + j] = cscale(zs, 0.25f);
         R1w[i * sc + j] = cscale(rs, 0.25f);
       }
     }
     __syncthreads();
+    if (l3) {
+      {  // restrict 1 -> 2 from the prefetched weights
+        constexpr int sf = wc1 + 1, sc = wc2 + 1;
+        const float2* __restrict__ const Zf = Zl[1];
+        const float2* __restrict__ const Rf = Rl[1];
+        float2* __restrict__ const Zc = Zl[2];
+        float2* __restrict__ const Rc = Rl[2];
+#pragma unroll
+        for (int t = 0; t < Q12; ++t) {
+          const int p = tid + t * NT, i = p / wc2, j = p % wc2;
+          float2 zs = czero(), rs = czero();
+#pragma unroll
+          for (int dy = 0; dy < 2; ++dy) {
+            const int lr = 2 * i + dy, c = 2 * j;
+            zs = cadd(zs, cscale(Zf[lr * sf + c], pf_wz1[t][dy].x));
+            rs = cadd(rs, cmul(make_float2(pf_wr1[t][dy].x, pf_wr1[t][dy].y), Rf[lr * sf + c]));
+            zs = cadd(zs, cscale(Zf[lr * sf + c + 1], pf_wz1[t][dy].y));
+            rs = cadd(rs, cmul(make_float2(pf_wr1[t][dy].z, pf_wr1[t][dy].w), Rf[lr * sf + c + 1]));
+          }
+          Zc[i * sc + j] = cscale(zs, 0.25f);
+          Rc[i * sc + j] = cscale(rs, 0.25f);
+        }
+      }
+      __syncthreads();
+      {  // coarsest level 2
+        constexpr int sl = wc2 + 1;
+        float2* __restrict__ const Zw = Zl[2];
+        const float2* __restrict__ const Rw = Rl[2];
+#pragma unroll
+        for (int t = 0; t < Q12; ++t) {
+          const int p = tid + t * NT, i = p / wc2, j = p % wc2;
+          const float2 z = Zw[i * sl + j];
+          Zw[i * sl + j] = cmul(pf_g2[t], csub(Rw[i * sl + j], cmul(pf_q2[t], z)));
+        }
+      }
+      if (halo) {
+        cl.sync();
+        fill_halo(2);
+      }
+      __syncthreads();
+      {  // back up to level 1
+        constexpr int sl = wc1 + 1, sc = wc2 + 1;
+        float2* __restrict__ const Zw = Zl[1];
+        const float2* __restrict__ const Rw = Rl[1];
+        const float2* __restrict__ const Zc = Zl[2];
+#pragma unroll
+        for (int t = 0; t < QUP; ++t) {
+          const int p = tid + t * NT, i = p / wc1, j = p % wc1;
+          const float2 pro = prolong_halo<float2>(Zc, sc, wc2, i, j, a.prolong);
+          const float2 zp = cadd(Zw[i * sl + j], pro);
+          Zw[i * sl + j] = cadd(pro, cmul(pf_g1[t], csub(Rw[i * sl + j], cmul(pf_q1[t], zp))));
+        }
+      }
+    } else {
     for (int l = 1; l + 1 < a.levels; ++l) {
       const int wf = M >> l, sf = wf + 1, hf = wf / C, wc = wf >> 1, hc = wc / C, sc = wc + 1;
       const float* Wz = a.lv.Wz[l];
@@ -1132,6 +1229,7 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
         Zw[i * sl + j] = cadd(pro, cmul(__ldcg(G + li), csub(Rw[i * sl + j], cmul(__ldcg(Q + li), zp))));
       }
     }
+    }  // generic levels
     if (halo) {
       cl.sync();
       fill_halo(1);
