@@ -12,6 +12,7 @@
 //   k_fft2<M>      batched 2-D DFT of natural-order tiles
 #include <cooperative_groups.h>
 #include <math.h>
+#include <stdint.h>
 
 #include "emg_fft.cuh"
 #include "emg_internal.h"
@@ -868,7 +869,7 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
   constexpr int N1 = TL::N1, N2 = TL::N2, PER = TL::PER, SLOTS = TL::SLOTS;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];  // 16-byte aligned: the update pass reads pixel pairs
   float2* rowbuf = sm;                     // H x SR: my patch rows
   float2* colbuf = sm + H * SR;            // M x SC: my storage columns (all rows); multigrid buffers later
   float2* zbuf = colbuf + M * SC;          // H x M: z_k on my rows (gathered once)
@@ -1247,8 +1248,53 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
   // the loop body stays small enough for the instruction cache.
   constexpr int UG0 = EMG_UPDATE_GROUP < PER ? EMG_UPDATE_GROUP : PER;
   constexpr int UG = PER % UG0 == 0 ? UG0 : 1;
+  // The common case (multigrid, joint step, ordered combine, no verify) runs a
+  // loop without the mode branches over pairs of adjacent pixels, with 16-byte
+  // probe loads and patch stores; the arithmetic per pixel is the same.
+  constexpr int UGP = UG >= 2 && PER % 2 == 0 ? UG / 2 : 0;
+  const bool pairs = UGP > 0 && a.levels > 1 && a.joint && !a.s_num && !a.verify && slot_ok &&
+                     ((reinterpret_cast<uintptr_t>(a.probe) | reinterpret_cast<uintptr_t>(zt) |
+                       reinterpret_cast<uintptr_t>(qt)) & 15) == 0;
+  if constexpr (UGP > 0) {
+    if (pairs) {
+      constexpr int PP = PER / 2;
 #pragma unroll 1
-  for (int t0 = 0; t0 < PER; t0 += UG) {
+      for (int t0 = 0; t0 < PP; t0 += UGP) {
+        float4 qv[UGP];
+#pragma unroll
+        for (int u = 0; u < UGP; ++u)
+          qv[u] = __ldg(reinterpret_cast<const float4*>(a.probe + row0 * M + 2 * (tid + (t0 + u) * NT)));
+#pragma unroll
+        for (int u = 0; u < UGP; ++u) {
+          const int p0 = 2 * (tid + (t0 + u) * NT);
+          const int lr = p0 / M, c0 = p0 % M, r = row0 + lr;
+          const float4 zk2 = *reinterpret_cast<const float4*>(zbuf + p0);
+          float2 zo[2], qo[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int c = c0 + h;
+            const float2 zk = h ? make_float2(zk2.z, zk2.w) : make_float2(zk2.x, zk2.y);
+            const float2 q = h ? make_float2(qv[u].z, qv[u].w) : make_float2(qv[u].x, qv[u].y);
+            const float2 R = rowbuf[lr * SR + c];
+            const float2 res = csub(R, cmul(q, zk));
+            const float a2 = cabs2(q);
+            const float den = fmaf(a.alpha, MQ - a2, a2);
+            const float2 g0 = den != 0.f ? cscale(cconj(q), __frcp_rn(den)) : czero();
+            const float2 pro = prolong_halo<float2>(Z1, M / 2 + 1, M / 2, lr, c, a.prolong);
+            const float2 zp = cadd(zk, pro);
+            const float2 zplus = cadd(zp, cmul(g0, csub(R, cmul(q, zp))));
+            const float2 qplus = cadd(q, cscale(cconjmul(zk, res), inv_mu));
+            zo[h] = geometric_mean_aligned_fast(zk, zplus);
+            qo[h] = geometric_mean_aligned_fast(q, qplus);
+          }
+          *reinterpret_cast<float4*>(zt + r * M + c0) = make_float4(zo[0].x, zo[0].y, zo[1].x, zo[1].y);
+          *reinterpret_cast<float4*>(qt + r * M + c0) = make_float4(qo[0].x, qo[0].y, qo[1].x, qo[1].y);
+        }
+      }
+    }
+  }
+#pragma unroll 1
+  for (int t0 = 0; t0 < (pairs ? 0 : PER); t0 += UG) {
   float2 qv[UG];
 #pragma unroll
   for (int u = 0; u < UG; ++u) qv[u] = __ldg(a.probe + row0 * M + tid + (t0 + u) * NT);
