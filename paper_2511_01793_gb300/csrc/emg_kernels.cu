@@ -1116,12 +1116,12 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
     }
     __syncthreads();
     if (l3) {
-      {  // restrict 1 -> 2 from the prefetched weights
+      {  // restrict 1 -> 2 from the prefetched weights, and at once the coarsest step
+         // on the same level-2 pixel (it needs nothing from other threads)
         constexpr int sf = wc1 + 1, sc = wc2 + 1;
         const float2* __restrict__ const Zf = Zl[1];
         const float2* __restrict__ const Rf = Rl[1];
         float2* __restrict__ const Zc = Zl[2];
-        float2* __restrict__ const Rc = Rl[2];
 #pragma unroll
         for (int t = 0; t < Q12; ++t) {
           const int p = tid + t * NT, i = p / wc2, j = p % wc2;
@@ -1134,20 +1134,9 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
             zs = cadd(zs, cscale(Zf[lr * sf + c + 1], pf_wz1[t][dy].y));
             rs = cadd(rs, cmul(make_float2(pf_wr1[t][dy].z, pf_wr1[t][dy].w), Rf[lr * sf + c + 1]));
           }
-          Zc[i * sc + j] = cscale(zs, 0.25f);
-          Rc[i * sc + j] = cscale(rs, 0.25f);
-        }
-      }
-      __syncthreads();
-      {  // coarsest level 2
-        constexpr int sl = wc2 + 1;
-        float2* __restrict__ const Zw = Zl[2];
-        const float2* __restrict__ const Rw = Rl[2];
-#pragma unroll
-        for (int t = 0; t < Q12; ++t) {
-          const int p = tid + t * NT, i = p / wc2, j = p % wc2;
-          const float2 z = Zw[i * sl + j];
-          Zw[i * sl + j] = cmul(pf_g2[t], csub(Rw[i * sl + j], cmul(pf_q2[t], z)));
+          const float2 z2 = cscale(zs, 0.25f), r2 = cscale(rs, 0.25f);
+          // coarsest level 2: correction c = G (R - Q z), stored over z
+          Zc[i * sc + j] = cmul(pf_g2[t], csub(r2, cmul(pf_q2[t], z2)));
         }
       }
       if (halo) {
