@@ -116,6 +116,16 @@ def test_context_free_calls_validate_arguments(lib):
     assert lib.emg_set_cluster(None, 2) == emg.EMG_EINVAL
     assert lib.emg_set_prep_fusion(None, 1) == emg.EMG_EINVAL
     assert lib.emg_debug_prep_wait_extra(None, 0) == emg.EMG_EINVAL
+    idx = (ctypes.c_int32 * 2)(0, 1)
+    assert lib.emg_shard_step(None, idx, 2, 0, 1, 0x10, 0x20, 0x30) == emg.EMG_EINVAL
+    assert lib.emg_shard_apply(None, idx, 2, 0x10, 0x20, 0x30) == emg.EMG_EINVAL
+    out = (ctypes.c_double * 5)()
+    assert lib.emg_aligned_errors(None, 0x10, 8, 8, 0x20, 0x30, 4, None, out, None) == emg.EMG_EINVAL
+    assert lib.emg_aligned_errors(0x10, 0x20, 0, 8, 0x30, 0x40, 4, None, out, None) == emg.EMG_EINVAL
+    assert lib.emg_aligned_errors(0x10, 0x20, 8, 8, 0x30, 0x40, 4, None, None, None) == emg.EMG_EINVAL
+    assert lib.emg_illuminated_region(None, 4, 0x10, 1, 8, 8, 0.1, 0x20, None) == emg.EMG_EINVAL
+    assert lib.emg_illuminated_region(0x10, 4, 0x20, 1, 8, 8, float("nan"), 0x30, None) == emg.EMG_EINVAL
+    assert lib.emg_illuminated_region(0x10, 4, 0x20, 0, 8, 8, 0.1, 0x30, None) == emg.EMG_EINVAL
     lib.emg_destroy(None)  # no-op
 
 
