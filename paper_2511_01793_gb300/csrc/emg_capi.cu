@@ -99,6 +99,11 @@ struct emg_ctx {
   int grad_chunk = 0;             // positions per gradient launch in use (0: not chosen yet)
   float2* d_gz = nullptr;         // [grad_chunk][m][m] when it exceeds the minibatch
   float2* d_gq = nullptr;
+  // second pair of gradient patch buffers: the sums of one chunk run on the
+  // side stream while the next chunk's patches are computed
+  float2* d_gz2 = nullptr;
+  float2* d_gq2 = nullptr;
+  cudaEvent_t ev_grad[3] = {nullptr, nullptr, nullptr};  // chunk computed; sums of buffer 0 / 1 done
   double* h_scalar = nullptr;     // pinned [64]
 
   // kernel timing (emg_set_profiling): CUDA events around each launch, per kernel kind
@@ -290,6 +295,10 @@ void free_all(emg_ctx* c) {
   cudaFree(c->d_own_probe);
   cudaFree(c->d_gz);
   cudaFree(c->d_gq);
+  cudaFree(c->d_gz2);
+  cudaFree(c->d_gq2);
+  for (cudaEvent_t& ev : c->ev_grad)
+    if (ev) cudaEventDestroy(ev);
   if (c->h_scalar) cudaFreeHost(c->h_scalar);
   emg::tc_work_destroy(c->tc);
   c->tc = nullptr;
@@ -723,7 +732,9 @@ emg_status set_minibatch_impl(emg_ctx* c, int32_t B) {
   // the gradient may have used the minibatch buffers for its patches
   cudaFree(c->d_gz);
   cudaFree(c->d_gq);
-  c->d_gz = c->d_gq = nullptr;
+  cudaFree(c->d_gz2);
+  cudaFree(c->d_gq2);
+  c->d_gz = c->d_gq = c->d_gz2 = c->d_gq2 = nullptr;
   c->grad_chunk = 0;
   drop_graphs(c);
   return EMG_OK;
@@ -1375,10 +1386,34 @@ emg_status emg_misfit_gradient(emg_ctx* c, const float* object, const float* pro
     c->grad_chunk = chunk;
   }
   const int B = c->grad_chunk;
-  float2* gz = c->d_gz ? c->d_gz : c->d_zt;
-  float2* gq = c->d_gq ? c->d_gq : c->d_qt;
-  for (int first = 0; first < N; first += B) {
+  const bool sums = grad_object || grad_probe;
+  // With the sums asked for and more than one chunk, the sums of chunk i run on
+  // the side stream while chunk i + 1's patches are computed into the other
+  // buffer pair; the sums stay in chunk order on the side stream, so the
+  // result is the same bitwise.  Without a second pair the chunks run in turn.
+  bool overlap = sums && N > B;
+  if (overlap && !c->d_gz2) {
+    const size_t bytes = (size_t)B * c->m * c->m * sizeof(float2);
+    if (cudaMalloc(&c->d_gz2, bytes) != cudaSuccess || cudaMalloc(&c->d_gq2, bytes) != cudaSuccess) {
+      cudaFree(c->d_gz2);
+      c->d_gz2 = nullptr;
+      cudaGetLastError();
+      overlap = false;
+    }
+  }
+  for (int j = 0; overlap && j < 3; ++j)
+    if (!c->ev_grad[j] && cudaEventCreateWithFlags(&c->ev_grad[j], cudaEventDisableTiming) != cudaSuccess) {
+      c->ev_grad[j] = nullptr;
+      cudaGetLastError();
+      overlap = false;
+    }
+  for (int first = 0, chunk = 0; first < N; first += B, ++chunk) {
     const int b = (N - first < B) ? N - first : B;
+    const int pair = overlap ? (chunk & 1) : 0;
+    float2* gz = pair ? c->d_gz2 : (c->d_gz ? c->d_gz : c->d_zt);
+    float2* gq = pair ? c->d_gq2 : (c->d_gq ? c->d_gq : c->d_qt);
+    // the pair is free once the sums of chunk - 2 (which used it) are done
+    if (overlap && chunk >= 2) EMG_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_grad[1 + pair], 0));
     emg::GradArgs ga{};
     ga.object = (const float2*)object;
     ga.probe = (const float2*)probe;
@@ -1393,7 +1428,12 @@ emg_status emg_misfit_gradient(emg_ctx* c, const float* object, const float* pro
     cudaError_t e = emg::launch_gradient(c->m, b, ga, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "k_gradc launch");
     c->launches[kKindOther] += 1;
-    if (grad_object || grad_probe) {
+    if (sums) {
+      const cudaStream_t rs = overlap ? c->side : c->stream;
+      if (overlap) {
+        EMG_CUDA(c, cudaEventRecord(c->ev_grad[0], c->stream));
+        EMG_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_grad[0], 0));
+      }
       emg::GradReduceArgs ra{};
       ra.pos = c->d_pos;
       ra.first = first;
@@ -1408,10 +1448,15 @@ emg_status emg_misfit_gradient(emg_ctx* c, const float* object, const float* pro
       ra.grad_probe = (float2*)grad_probe;
       ra.tiles_x = (c->n_cols + emg::kApplyTile - 1) / emg::kApplyTile;
       ra.tiles_y = (c->n_rows + emg::kApplyTile - 1) / emg::kApplyTile;
-      e = emg::launch_grad_reduce(ra, c->stream);
+      e = emg::launch_grad_reduce(ra, rs);
       if (e != cudaSuccess) return cuda_fail(c, e, "k_grad_reduce launch");
       c->launches[kKindOther] += 1;
+      if (overlap) EMG_CUDA(c, cudaEventRecord(c->ev_grad[1 + pair], c->side));
     }
+  }
+  if (overlap) {  // the caller's stream sees every sum
+    EMG_CUDA(c, cudaEventRecord(c->ev_grad[0], c->side));
+    EMG_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_grad[0], 0));
   }
   if (misfit) {
     cudaError_t e = emg::launch_sum(c->d_phi, N, 1.0, c->d_scalar, c->stream);
@@ -1430,7 +1475,9 @@ emg_status emg_set_gradient_chunk(emg_ctx* c, int32_t positions) {
   EMG_CUDA(c, cudaStreamSynchronize(c->stream));
   cudaFree(c->d_gz);
   cudaFree(c->d_gq);
-  c->d_gz = c->d_gq = nullptr;
+  cudaFree(c->d_gz2);
+  cudaFree(c->d_gq2);
+  c->d_gz = c->d_gq = c->d_gz2 = c->d_gq2 = nullptr;
   c->grad_chunk_req = positions;
   c->grad_chunk = 0;
   return EMG_OK;

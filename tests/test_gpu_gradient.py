@@ -46,6 +46,29 @@ def test_gradient_matches_the_oracle(lib, torch, m, chunk):
     assert rel_err(gq, gq_o) <= 1e-5
 
 
+def test_chunked_gradient_sums_are_bitwise_repeatable(lib, torch):
+    """Several chunks: the sums of one chunk run beside the next chunk's patches on
+    two buffer pairs.  Calls in a row, and a call after a misfit-only one, give
+    bitwise the same gradients."""
+    m = 64
+    case = Case(n=2 * m + 40, m=m, side=5, noise_peak=1e4, seed=140)
+    ctx = make_context(lib, case, oracle_params(minibatch=6))
+    lib.emg_set_gradient_chunk(ctx.ctx, 5)               # 29 positions: 6 chunks
+    first = _gpu_gradient(lib, torch, ctx, case.z0, case.q0)
+    second = _gpu_gradient(lib, torch, ctx, case.z0, case.q0)
+    zd = torch.from_numpy(c64(case.z0)).cuda()
+    qd = torch.from_numpy(c64(case.q0)).cuda()
+    lib.emg_misfit_gradient(ctx.ctx, zd.data_ptr(), qd.data_ptr(), 0, 0, True)
+    third = _gpu_gradient(lib, torch, ctx, case.z0, case.q0)
+    ctx.close()
+    for other in (second, third):
+        assert other[0] == first[0]
+        assert np.array_equal(other[1], first[1]) and np.array_equal(other[2], first[2])
+    phi_o, gz_o, gq_o = O.misfit_gradients(case.q0.astype(np.complex128), case.z0.astype(np.complex128),
+                                           case.pos, case.a64)
+    assert rel_err(first[1], gz_o) <= 1e-5 and rel_err(first[2], gq_o) <= 1e-5
+
+
 def test_gradient_matches_central_differences(lib, torch):
     """Central differences (h = 1e-3) of the FP64 misfit at the same point."""
     case = Case(n=104, m=32, side=4, noise_peak=1e4, seed=9)
