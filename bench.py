@@ -781,12 +781,32 @@ def run_gpu_prec(args, world, rank, local):
     t_e2e = max_over_ranks(t_e2e, world)
     tc = res["bf16x3"]
     dft_ms, dft_launches = tc["prof"]["dft"]
-    # executed MMA work of the four GEMM passes: 2 (b m) (2m) (2m) flops per pass and product, 3 products
-    flops_epoch = 4 * 2 * N * m * (2 * m) * (2 * m) * 3
-    achieved = flops_epoch * 2 / (dft_ms / 1e3) / 1e12
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    timing = (f"CUDA events around each minibatch's DFT chain over 2 epochs "
+              f"({dft_ms / 2:.3f} ms/epoch of {tc['ms_per_epoch']:.3f})")
+    if emg.emg_dft_bf16x3_form(m):
+        # radix-16 passes: HBM-bound.  Algorithmic bytes per pixel and position:
+        # psi (object read 8, split write 8), three split passes (read 8, write 8;
+        # the modulus pass also reads a_k, 4), the last pass (read 8, FP32 write 8)
+        bytes_mb = B * m * m * (16 + 16 + 20 + 16 + 16)
+        achieved = bytes_mb * (N / B) * 2 / (dft_ms / 1e3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 5),
+                    "peak_source": "measured (copy)" if "hbm_gbs" in peaks else "fallback",
+                    "traffic": None, "kernel": "k_tc_rows16 + k_tc_fft16 x4 (radix-16 tensor-core DFT chain)",
+                    "bytes_per_minibatch": bytes_mb, "timing": timing}
+    else:
+        # executed MMA work of the four GEMM passes: 2 (b m) (2m) (2m) flops per pass and product, 3 products
+        flops_epoch = 4 * 2 * N * m * (2 * m) * (2 * m) * 3
+        achieved = flops_epoch * 2 / (dft_ms / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        roofline = {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
+                    "frac": round(achieved / peak, 5),
+                    "peak_source": "measured (bf16, sustained)" if peaks else "fallback",
+                    "traffic": None, "kernel": "k_tc_dft x4 + k_tc_psi (dense tensor-core DFT chain)",
+                    "flops_per_minibatch": 4 * 2 * B * m * (2 * m) * (2 * m) * 3, "timing": timing}
     line = {
         "metric": "scan positions/sec per eMAGPIE epoch (DFT pair on tensor cores, BF16 x3 split)",
         "value": tc["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -802,12 +822,7 @@ def run_gpu_prec(args, world, rank, local):
                                                                                           qn.nbytes),
                 "d2h_bytes_per_step": int(zn.nbytes + qn.nbytes + 8)},
         "gpu_launches": sum(v[1] for v in tc["counts"].values()),
-        "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
-                     "frac": round(achieved / peak, 5), "peak_source": "measured (bf16, sustained)",
-                     "traffic": None, "kernel": "k_tc_dft x4 + k_tc_psi (tensor-core DFT chain)",
-                     "flops_per_minibatch": 4 * 2 * B * m * (2 * m) * (2 * m) * 3,
-                     "timing": f"CUDA events around each minibatch's DFT chain over 2 epochs "
-                               f"({dft_ms / 2:.3f} ms/epoch of {tc['ms_per_epoch']:.3f})"},
+        "roofline": roofline,
         "clocks": tc["clocks"],
     }
     if rank != 0:

@@ -366,12 +366,17 @@ emg_status emg_fft2(const float* in, float* out, int32_t m, int32_t count, int32
 
 /*
  * The same batched 2-D DFT on the tensor cores (the precision variant of the
- * FFT pair of Sec. 2.1): each 1-D pass is a GEMM of the rows of all tiles with
- * the 2m x 2m real matrix of x -> x F (or x conj(F)) in BF16, every operand
- * split into high and low parts (x = xh + xl, xh = bf16(x), xl = bf16(x - xh))
- * and the products xh yh + xh yl + xl yh accumulated in FP32.  The relative
- * error per transform is of order 3 u^2 per pass, u = 2^-8 (about 1e-4 in the
- * L2 norm), against about 1e-7 for emg_fft2.
+ * FFT pair of Sec. 2.1).  Every operand is split into high and low parts in
+ * BF16 (x = xh + xl, xh = bf16(x), xl = bf16(x - xh)) and the products
+ * xh yh + xh yl + xl yh accumulate in FP32.  At m = 128 (and at m = 256 with
+ * the environment variable EMG_TC_RADIX16=0) each 1-D pass is one GEMM of the
+ * rows of all tiles with the 2m x 2m real matrix of x -> x F (or x conj(F)):
+ * relative error of order 3 u^2 per pass, u = 2^-8.  At m = 256 each 1-D
+ * pass is by default a radix-16 pass (256 = 16 x 16): two 16-point DFT
+ * products with an FP32 twiddle multiply between them, 1/8 of the flops of the
+ * dense GEMM and about twice its error (about 2e-4 in the L2 norm per 2-D
+ * transform, against about 1e-7 for emg_fft2); emg_dft_bf16x3_form reports
+ * which form runs.
  *  in, out  device complex64 [count][m][m], natural order; may not alias
  *  m        128 or 256 (EMG_ENOTSUP otherwise)
  * Allocates and frees its split buffers and synchronises the stream.
@@ -379,6 +384,14 @@ emg_status emg_fft2(const float* in, float* out, int32_t m, int32_t count, int32
  */
 emg_status emg_dft2_bf16x3(const float* in, float* out, int32_t m, int32_t count, int32_t inverse,
                            emg_stream_t stream);
+
+/*
+ * Which form the tensor-core DFT of size m takes in this process (the
+ * variable EMG_TC_RADIX16 is read once per process): *radix16 = 1 for radix-16
+ * passes (m = 256 by default), 0 for dense GEMM passes.  EMG_ENOTSUP if m is
+ * not 128 or 256, EMG_EINVAL if radix16 is NULL.  Host only; launches nothing.
+ */
+emg_status emg_dft_bf16x3_form(int32_t m, int32_t* radix16);
 
 /*
  * Check of the failure path of the tensor-core kernel's waits: one CTA waits,

@@ -26,7 +26,7 @@ __all__ = [
     "emg_create", "emg_set_intensity", "emg_bind_state", "emg_normalize_probe",
     "emg_step_minibatch", "emg_position_stats", "emg_set_verify", "emg_run_epochs", "emg_misfit",
     "emg_set_epoch", "emg_schedule_permutation", "emg_stopping_epoch", "emg_run_until", "emg_reconstruct_host",
-    "emg_simulate_intensity", "emg_fft2", "emg_dft2_bf16x3", "emg_aligned_errors", "emg_shard_step",
+    "emg_simulate_intensity", "emg_fft2", "emg_dft2_bf16x3", "emg_dft_bf16x3_form", "emg_aligned_errors", "emg_shard_step",
     "emg_shard_apply",
     "emg_illuminated_region", "emg_step_minibatch_noalloc", "emg_misfit_gradient",
     "emg_set_cluster", "emg_set_prep_fusion", "emg_debug_prep_wait_extra", "emg_set_gradient_chunk", "emg_autotune", "emg_set_minibatch", "emg_set_scatter",
@@ -111,6 +111,7 @@ _SIGS = {
     "emg_run_until": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                      ctypes.POINTER(ctypes.c_int32), _F64P]),
     "emg_dft2_bf16x3": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP]),
+    "emg_dft_bf16x3_form": (ctypes.c_int, [ctypes.c_int32, _I32P]),
     "emg_step_minibatch_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_int32,
                                                   _VP, _VP, ctypes.c_int32, _I32P, ctypes.c_int32,
                                                   ctypes.POINTER(EmgParams), _VP]),
@@ -353,6 +354,13 @@ def emg_illuminated_region(probe_ref_ptr: int, m: int, pos_ptr: int, n_pos: int,
 def emg_dft2_bf16x3(in_ptr: int, out_ptr: int, m: int, count: int, inverse: bool, stream: int = 0) -> None:
     _check(load().emg_dft2_bf16x3(in_ptr, out_ptr, m, count, int(bool(inverse)), _VP(stream)),
            "emg_dft2_bf16x3")
+
+
+def emg_dft_bf16x3_form(m: int) -> bool:
+    """True if the tensor-core DFT of size m runs as radix-16 passes in this process, False if dense."""
+    v = ctypes.c_int32(0)
+    _check(load().emg_dft_bf16x3_form(m, ctypes.byref(v)), "emg_dft_bf16x3_form")
+    return bool(v.value)
 
 
 def emg_step_minibatch_noalloc(object_ptr: int, n_rows: int, n_cols: int, probe_ptr: int, m: int,

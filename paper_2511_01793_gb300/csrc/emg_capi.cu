@@ -1361,6 +1361,13 @@ emg_status emg_dft2_bf16x3(const float* in, float* out, int32_t m, int32_t count
   return flag ? EMG_ETIMEOUT : EMG_OK;
 }
 
+emg_status emg_dft_bf16x3_form(int32_t m, int32_t* radix16) {
+  if (!radix16) return EMG_EINVAL;
+  if (!emg::tc_supported(m)) return EMG_ENOTSUP;
+  *radix16 = emg::tc_radix16(m) ? 1 : 0;
+  return EMG_OK;
+}
+
 emg_status emg_misfit_gradient(emg_ctx* c, const float* object, const float* probe, float* grad_object,
                                float* grad_probe, double* misfit) {
   NvtxRange nvtx_range("emg_misfit_gradient");

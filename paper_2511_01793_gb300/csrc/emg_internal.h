@@ -210,6 +210,7 @@ struct TcStepArgs {
   double* partial;              // [b][tc_tiles_per_position(m)] out: sums of (|Psi| - a)^2
 };
 bool tc_supported(int m);
+bool tc_radix16(int m);  // m = 256 and EMG_TC_RADIX16 is not "0..."
 cudaError_t tc_work_create(TcWork** out, int m, int cap);
 void tc_work_destroy(TcWork* w);
 int* tc_error_flag(TcWork* w);

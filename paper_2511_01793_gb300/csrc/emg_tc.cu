@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -168,15 +169,15 @@ __device__ __forceinline__ void load16(const float* p, float (&v)[16]) {
   }
 }
 
-__device__ __forceinline__ uint32_t bf16_bits(float x) {
-  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+// (re, im) -> high and low bf16 pairs: hi = bf16(x), lo = bf16(x - hi), re in the
+// low half of each word (one packed conversion per pair).
+__device__ __forceinline__ uint32_t pack_bf16x2(float re, float im) {
+  const __nv_bfloat162 p = __floats2bfloat162_rn(re, im);
+  return *reinterpret_cast<const uint32_t*>(&p);
 }
-
-// (re, im) -> high and low bf16 pairs: hi = bf16(x), lo = bf16(x - hi).
 __device__ __forceinline__ void split_pair(float re, float im, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat16 hr = __float2bfloat16_rn(re), hm = __float2bfloat16_rn(im);
-  hi = (uint32_t)__bfloat16_as_ushort(hr) | ((uint32_t)__bfloat16_as_ushort(hm) << 16);
-  lo = bf16_bits(re - __bfloat162float(hr)) | (bf16_bits(im - __bfloat162float(hm)) << 16);
+  hi = pack_bf16x2(re, im);
+  lo = pack_bf16x2(re - __uint_as_float(hi << 16), im - __uint_as_float(hi & 0xFFFF0000u));
 }
 
 struct TcPassArgs {
@@ -190,6 +191,7 @@ struct TcPassArgs {
   const int32_t* order;     // modulus mode: position of tile kb
   double* partial;          // modulus mode: sum (|Psi| - a)^2 per output tile and epilogue warp
   int* err;                 // set to 1 when a bounded wait gives up
+  int rows16;               // radix-16 pass: output row k stored at r16_perm(k)
 };
 
 // Epilogue modes.
@@ -437,7 +439,409 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
-// Complex64 tiles -> high / low bf16 pairs (same order).
+// ---------------------------------------------------------------------------
+// Radix-16 pass (m = 256): each 1-D DFT of length 256 = 16 x 16 as two 16-point
+// DFT GEMMs with a twiddle multiply between them, both on chip:
+//   n = 16 n1 + n2, k = k1 + 16 k2,
+//   Y[n2][k1] = sum_n1 x[16 n1 + n2] W16^(n1 k1)            (stage 1)
+//   X[k1 + 16 k2] = sum_n2 W16^(n2 k2) W256^(n2 k1) Y[n2][k1]  (stage 2)
+// Rows hold their elements in digit-swapped order (logical index 16 n1 + n2 at
+// position 16 n2 + n1), so the stage-1 input of each n2 is 32 contiguous bf16:
+// one TMA box of 128 rows, exactly the A chunk of the dense pass.  Per block of
+// 128 rows, warp 1 issues the stage-1 MMAs of all 16 n2 (N = 16 per half of the
+// k1 range) into all 512 TMEM columns; the epilogue warps multiply by the
+// twiddles, split into BF16 high and low parts and write the stage-2 operands
+// (8 k1 at a time) into shared memory in the same 64-byte swizzled layout that
+// TMA produces; warp 1 then issues the stage-2 MMAs (N = 32) into the columns
+// just drained, and the epilogue warps write the outputs.  The same 32 x 32
+// real matrix of the 16-point DFT serves both stages.  Every wait is bounded.
+constexpr int kR16Stages = 4;
+constexpr int kR16Tile = kBM * kBK * 2;                   // 8 KB: 128 rows x 32 bf16
+constexpr int kR16StageBytes = 2 * kR16Tile;              // A hi, A lo
+constexpr int kR16BBytes = 32 * kBK * 2;                  // 2 KB: the 32 x 32 matrix, hi or lo
+constexpr int kR16A2Bytes = 8 * kR16Tile;                 // 64 KB: stage-2 operands of 8 k1, hi or lo
+constexpr int kR16Smem = kR16Stages * kR16StageBytes + 2 * kR16BBytes + 2 * kR16A2Bytes + 1024;
+// Chunks kR16XFirst .. kR16XFirst + 7 of a block are staged in the stage-2 operand
+// area (free from the end of the previous block's stage-2 MMAs until the
+// epilogue writes it), so that most of a block's loads are in flight while the
+// previous block's outputs drain; the others go through the ring.
+constexpr int kR16XChunks = 2 * kR16A2Bytes / kR16StageBytes;  // 8
+constexpr int kR16XFirst = 4;
+static_assert(kR16XFirst + kR16XChunks <= 16, "staged chunks within the 16 of a block");
+constexpr uint32_t kIdescN16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(16 >> 3) << 17) |
+                               ((uint32_t)(kBM >> 4) << 24);
+constexpr uint32_t kIdescN32 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(32 >> 3) << 17) |
+                               ((uint32_t)(kBM >> 4) << 24);
+
+// W_256^j, j = 0..255, filled on the host in FP64 (once per device).
+__constant__ float2 c_tw256[256];
+
+__device__ __forceinline__ void umma_bf16_n(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// 16 consecutive FP32 columns of the warp's 32 TMEM lanes; completes with tmem_ld_wait.
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+// Position of logical element n = 16 n1 + n2 in a digit-swapped row (an involution).
+__host__ __device__ __forceinline__ int r16_perm(int n) { return ((n & 15) << 4) | (n >> 4); }
+__device__ __forceinline__ bool r16_staged(int n2) { return n2 >= kR16XFirst && n2 < kR16XFirst + kR16XChunks; }
+
+template <int EPI>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_fft16(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+               const TcPassArgs a, const int inverse) {
+  static_assert(EPI != kEpiF32, "the radix-16 pass writes transposed outputs only");
+  extern __shared__ uint8_t tc_smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[kR16Stages];   // stage-1 operands of one n2 landed
+  __shared__ __align__(8) uint64_t empty_bar[kR16Stages];  // ... and consumed by their MMAs
+  __shared__ __align__(8) uint64_t x_bar[kR16XChunks];      // chunks staged in the stage-2 operand area landed
+  __shared__ __align__(8) uint64_t b_bar;                   // the DFT matrix landed
+  __shared__ __align__(8) uint64_t d1_bar;                  // stage-1 accumulators complete
+  __shared__ __align__(8) uint64_t a2_bar[2];               // stage-2 operands of a k1 half written
+  __shared__ __align__(8) uint64_t s2_bar[2];               // stage-2 accumulators of a half complete
+  __shared__ __align__(8) uint64_t acce_bar;                // all accumulators drained
+  __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t raw = smem_u32(tc_smem_raw);
+  const uint32_t ring = (raw + 1023u) & ~1023u;
+  const uint32_t bsm = ring + kR16Stages * kR16StageBytes;  // B hi, then B lo
+  const uint32_t a2h = bsm + 2 * kR16BBytes;                // 8 tiles of stage-2 A, hi
+  const uint32_t a2l = a2h + kR16A2Bytes;                   // ... lo
+  const int m = a.m;
+  const int n_blocks = a.m_tiles;
+
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < kR16Stages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+#pragma unroll
+    for (int s = 0; s < kR16XChunks; ++s) mbar_init(&x_bar[s], 1);
+    mbar_init(&b_bar, 1);
+    mbar_init(&d1_bar, 1);
+    mbar_init(&a2_bar[0], kEpiWarps);
+    mbar_init(&a2_bar[1], kEpiWarps);
+    mbar_init(&s2_bar[0], 1);
+    mbar_init(&s2_bar[1], 1);
+    mbar_init(&acce_bar, kEpiWarps);
+    mbar_init(&drain_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");  // visible to the async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // the 16-point DFT matrix (32 x 32 real, K-major), once per CTA
+      mbar_expect_tx(&b_bar, 2 * kR16BBytes);
+      tma_load_2d(bsm, &mBh, &b_bar, 0, 0);
+      tma_load_2d(bsm + kR16BBytes, &mBl, &b_bar, 0, 0);
+      uint32_t it = 0;                // ring slots filled so far
+      int x_local = -1, x_count = 0;  // block and count of the chunks last staged in the operand area
+      int local = 0;
+      for (int blk = blockIdx.x; blk < n_blocks && !abort_sh; blk += gridDim.x, ++local) {
+        for (int n2 = 0; n2 < 16; ++n2) {
+          uint32_t st;
+          uint64_t* bar;
+          if (r16_staged(n2)) {
+            // the operand area is free once the previous block's stage-2 MMAs are complete
+            if (n2 == kR16XFirst && local > 0 && !mbar_wait(&s2_bar[1], (local - 1) & 1, &abort_sh)) {
+              abort_sh = 1;
+              atomicExch(a.err, 1);
+              break;
+            }
+            st = a2h + (uint32_t)(n2 - kR16XFirst) * kR16StageBytes;
+            bar = &x_bar[n2 - kR16XFirst];
+            if (x_local != local) x_count = 0;
+            x_local = local;
+            ++x_count;
+          } else {
+            const uint32_t s = it % kR16Stages;
+            if (it >= kR16Stages && !mbar_wait(&empty_bar[s], ((it / kR16Stages) + 1) & 1, &abort_sh)) {
+              abort_sh = 1;
+              atomicExch(a.err, 1);
+              break;
+            }
+            st = ring + s * kR16StageBytes;
+            bar = &full_bar[s];
+            ++it;
+          }
+          mbar_expect_tx(bar, kR16StageBytes);
+          tma_load_2d(st, &mAh, bar, n2 * kBK, blk * kBM);
+          tma_load_2d(st + kR16Tile, &mAl, bar, n2 * kBK, blk * kBM);
+        }
+      }
+      if (abort_sh) {  // let the copies already issued land before the CTA exits
+        const volatile int never = 0;
+        mbar_wait(&b_bar, 0, &never);
+        for (uint32_t j = it > kR16Stages ? it - kR16Stages : 0; j < it; ++j)
+          mbar_wait(&full_bar[j % kR16Stages], (j / kR16Stages) & 1, &never);
+        for (int j = 0; j < x_count; ++j) mbar_wait(&x_bar[j], x_local & 1, &never);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = mbar_wait(&b_bar, 0, &abort_sh);
+      uint32_t it = 0;
+      int local = 0;
+      for (int blk = blockIdx.x; ok && blk < n_blocks; blk += gridDim.x, ++local) {
+        if (local > 0 && !mbar_wait(&acce_bar, (local - 1) & 1, &abort_sh)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // stage 1: for each n2, a 16-point DFT of the 128 rows' n1 elements;
+        // half h of the k1 range lands in columns h * 256 + n2 * 16
+        for (int n2 = 0; n2 < 16; ++n2) {
+          const bool staged = r16_staged(n2);
+          const uint32_t s = it % kR16Stages;
+          if (!mbar_wait(staged ? &x_bar[n2 - kR16XFirst] : &full_bar[s],
+                         staged ? (uint32_t)(local & 1) : (it / kR16Stages) & 1, &abort_sh)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st =
+              staged ? a2h + (uint32_t)(n2 - kR16XFirst) * kR16StageBytes : ring + s * kR16StageBytes;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t d = tmem + (uint32_t)(h * 256 + n2 * 16);
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+              const uint64_t ah = sw_desc(st + kk * 32), al = sw_desc(st + kR16Tile + kk * 32);
+              const uint64_t bh = sw_desc(bsm + h * 1024 + kk * 32);
+              const uint64_t bl = sw_desc(bsm + kR16BBytes + h * 1024 + kk * 32);
+              umma_bf16_n(d, ah, bh, kIdescN16, kk != 0);
+              umma_bf16_n(d, ah, bl, kIdescN16, 1);
+              umma_bf16_n(d, al, bh, kIdescN16, 1);
+            }
+          }
+          if (!staged) {
+            umma_commit(&empty_bar[s]);
+            ++it;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&d1_bar);
+        // stage 2, one k1 half at a time: 16-point DFTs over n2 into columns h * 256 + j * 32
+        for (int h = 0; h < 2; ++h) {
+          if (!mbar_wait(&a2_bar[h], local & 1, &abort_sh)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll 1
+          for (int j = 0; j < 8; ++j) {
+            const uint32_t d = tmem + (uint32_t)(h * 256 + j * 32);
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+              const uint64_t ah = sw_desc(a2h + j * kR16Tile + kk * 32), al = sw_desc(a2l + j * kR16Tile + kk * 32);
+              const uint64_t bh = sw_desc(bsm + kk * 32), bl = sw_desc(bsm + kR16BBytes + kk * 32);
+              umma_bf16_n(d, ah, bh, kIdescN32, kk != 0);
+              umma_bf16_n(d, ah, bl, kIdescN32, 1);
+              umma_bf16_n(d, al, bh, kIdescN32, 1);
+            }
+          }
+          umma_commit(&s2_bar[h]);
+        }
+      }
+      if (!ok) {
+        abort_sh = 1;
+        atomicExch(a.err, 1);
+        umma_commit(&drain_bar);  // every MMA issued so far completes before the TMEM is freed
+        const volatile int never = 0;
+        mbar_wait(&drain_bar, 0, &never);
+      }
+    }
+  } else {
+    const int q = warp & 3;            // TMEM lane quadrant of this warp
+    const int ew = warp - 2;           // epilogue warp 0 .. 7
+    const int hw = ew >> 2;            // which half of the n2 (stage 1) or of the k1 (stage 2) range
+    const int t = q * 32 + lane;       // row within the block = TMEM lane
+    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+    const float tsign = inverse ? -1.f : 1.f;
+    int local = 0;
+    bool alive = true;
+    for (int blk = blockIdx.x; alive && blk < n_blocks; blk += gridDim.x, ++local) {
+      const int grow = blk * kBM + t, kb = grow / m, sr = grow % m;  // stored row sr of tile kb
+      bool got = mbar_wait(&d1_bar, local & 1, &abort_sh);
+      if (!__all_sync(0xffffffffu, got)) {
+        alive = false;
+        break;
+      }
+      tc_fence_after();
+      // stage-1 results -> twiddled, split stage-2 operands (row t; my 8 n2: chunks 2 hw, 2 hw + 1)
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1) {  // the stage-2 operand buffer is free once the half-0 MMAs are done
+          got = mbar_wait(&s2_bar[0], local & 1, &abort_sh);
+          if (!__all_sync(0xffffffffu, got)) {
+            alive = false;
+            break;
+          }
+          tc_fence_after();
+        }
+#pragma unroll 1
+        for (int g = 0; g < 2; ++g) {
+          const int n2b = 8 * hw + 4 * g, c = n2b >> 2;
+          uint32_t v[4][16];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) tmem_ld16_issue(tl + (uint32_t)(h * 256 + (n2b + i) * 16), v[i]);
+          tmem_ld_wait();
+          const uint32_t off = (uint32_t)((t >> 3) * 512 + (t & 7) * 64 + ((c ^ ((t >> 1) & 3)) << 4));
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int k1 = 8 * h + j;
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const float2 w = c_tw256[(n2b + i) * k1];
+              const float re = __uint_as_float(v[i][2 * j]), im = __uint_as_float(v[i][2 * j + 1]);
+              const float wi = tsign * w.y;
+              split_pair(re * w.x - im * wi, re * wi + im * w.x, hi[i], lo[i]);
+            }
+            sts128(a2h + j * kR16Tile + off, hi[0], hi[1], hi[2], hi[3]);
+            sts128(a2l + j * kR16Tile + off, lo[0], lo[1], lo[2], lo[3]);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the MMAs read these operands
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a2_bar[h]);  // one arrival per epilogue warp
+      }
+      if (!alive) break;
+      // stage-2 results: X[k1 + 16 k2], my 4 k1 of each half
+      float acc = 0.f;
+      // modulus: the 16 amplitudes of the next (h, jj) step are loaded one step ahead
+      const float* amp_tile = nullptr;
+      float am[16], am_next[16];
+      if constexpr (EPI == kEpiModulus) {
+        amp_tile = a.amp_t + (size_t)a.order[kb] * m * m + sr;
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+          const int k = 4 * hw + 16 * k2;  // h = 0, jj = 0
+          am_next[k2] = __ldg(amp_tile + (size_t)(a.rows16 ? r16_perm(k) : k) * m);
+        }
+      }
+      for (int h = 0; h < 2; ++h) {
+        got = mbar_wait(&s2_bar[h], local & 1, &abort_sh);
+        if (!__all_sync(0xffffffffu, got)) {
+          alive = false;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll 1
+        for (int jj = 0; jj < 4; ++jj) {
+          const int j = 4 * hw + jj, k1 = 8 * h + j;
+          float v[32];
+          if constexpr (EPI == kEpiModulus) {
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) am[k2] = am_next[k2];
+            const int step = 4 * h + jj + 1;  // the next step, if any
+            if (step < 8) {
+              const int k1n = 8 * (step >> 2) + 4 * hw + (step & 3);
+#pragma unroll
+              for (int k2 = 0; k2 < 16; ++k2) {
+                const int k = k1n + 16 * k2;
+                am_next[k2] = __ldg(amp_tile + (size_t)(a.rows16 ? r16_perm(k) : k) * m);
+              }
+            }
+          }
+          __syncwarp();
+          tmem_ld32(tl + (uint32_t)(h * 256 + j * 32), v);
+          // transposed outputs: frequency k = k1 + 16 k2 of stored input row sr goes to
+          // position sr of output row k (r16_perm(k) with rows16); a warp writes 128 contiguous bytes
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) {
+            const int k = k1 + 16 * k2;
+            const size_t o = ((size_t)kb * m + (a.rows16 ? r16_perm(k) : k)) * m + sr;
+            float re = v[2 * k2], im = v[2 * k2 + 1];
+            if constexpr (EPI == kEpiF32T) {
+              a.out_f32[o] = make_float2(re * a.scale, im * a.scale);
+            } else {
+              if constexpr (EPI == kEpiModulus) {
+                const float p2 = re * re + im * im;
+                if (p2 > 0.f) {
+                  const float inv = rsqrtf(p2);
+                  const float dm = fmaf(p2, inv, -am[k2]);
+                  acc = fmaf(dm, dm, acc);
+                  const float f = am[k2] * inv * a.scale;
+                  re *= f;
+                  im *= f;
+                } else {
+                  acc = fmaf(am[k2], am[k2], acc);
+                  re = am[k2] * a.scale;
+                  im = 0.f;
+                }
+              }
+              uint32_t hv, lv;
+              split_pair(re, im, hv, lv);
+              a.out_hi[o] = hv;
+              a.out_lo[o] = lv;
+            }
+          }
+        }
+      }
+      if (!alive) break;
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce_bar);  // one arrival per epilogue warp
+      if constexpr (EPI == kEpiModulus) {
+        double dsum = (double)acc;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, off);
+        if (lane == 0) a.partial[(size_t)blk * kEpiWarps + ew] = dsum;
+      }
+    }
+    if (!alive && lane == 0) {
+      abort_sh = 1;
+      atomicExch(a.err, 1);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// Complex64 -> high / low bf16 pairs, element by element.
 __global__ void __launch_bounds__(256) k_tc_split(const float2* __restrict__ in, uint32_t* __restrict__ hi,
                                                   uint32_t* __restrict__ lo, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -463,7 +867,7 @@ __global__ void __launch_bounds__(256) k_tc_psi(const float2* __restrict__ objec
     const int orow = pos[2 * k] + r, ocol = pos[2 * k + 1] + c;
     float2 z = make_float2(0.f, 0.f);
     if (orow >= 0 && orow < n_rows && ocol >= 0 && ocol < n_cols) z = object[(size_t)orow * n_cols + ocol];
-    const float2 q = probe[p];
+    const float2 q = probe[r * m + c];
     uint32_t h, l;
     split_pair(q.x * z.x - q.y * z.y, q.x * z.y + q.y * z.x, h, l);
     hi[i] = h;
@@ -471,7 +875,57 @@ __global__ void __launch_bounds__(256) k_tc_psi(const float2* __restrict__ objec
   }
 }
 
-// a_k^T[v][u] = sqrt(max(d_k[u][v], 0)).
+// Radix-16 layout (m = 256): tiles with rows and elements digit-swapped.  Each
+// block permutes kR16Rows rows at a time: they are read in natural order
+// (coalesced, all loads of a thread in flight together), permuted in shared
+// memory (padded by one word per 16 against bank conflicts) and written in
+// stored order (coalesced).  With object == nullptr the rows come from `in`
+// (tc_dft2); otherwise they are psi_k = Q . P_k z of minibatch slot kb.
+constexpr int kR16Rows = 4;
+__global__ void __launch_bounds__(256) k_tc_rows16(const float2* __restrict__ in, const float2* __restrict__ object,
+                                                   const float2* __restrict__ probe, const int32_t* __restrict__ pos,
+                                                   const int32_t* __restrict__ order, int n_rows, int n_cols,
+                                                   int n_tiles, uint32_t* __restrict__ hi, uint32_t* __restrict__ lo) {
+  constexpr int m = 256, R = kR16Rows;
+  __shared__ uint32_t sh[R][2][m + m / 16];
+  const int c = threadIdx.x;
+  const int pc = r16_perm(c);
+  for (int row0 = blockIdx.x * R; row0 < n_tiles * m; row0 += gridDim.x * R) {  // m is a multiple of R
+    float2 x[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int row = row0 + i, kb = row / m, r = row % m;
+      if (object == nullptr) {
+        x[i] = in[(size_t)row * m + c];
+      } else {
+        const int k = order[kb];
+        const int orow = pos[2 * k] + r, ocol = pos[2 * k + 1] + c;
+        float2 z = make_float2(0.f, 0.f);
+        if (orow >= 0 && orow < n_rows && ocol >= 0 && ocol < n_cols) z = object[(size_t)orow * n_cols + ocol];
+        const float2 q = probe[r * m + c];
+        x[i] = make_float2(q.x * z.x - q.y * z.y, q.x * z.y + q.y * z.x);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      uint32_t h, l;
+      split_pair(x[i].x, x[i].y, h, l);
+      sh[i][0][pc + (pc >> 4)] = h;
+      sh[i][1][pc + (pc >> 4)] = l;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int row = row0 + i, kb = row / m, r = row % m;
+      const size_t o = ((size_t)kb * m + r16_perm(r)) * m + c;
+      hi[o] = sh[i][0][c + (c >> 4)];
+      lo[o] = sh[i][1][c + (c >> 4)];
+    }
+    __syncthreads();
+  }
+}
+
+// The amplitudes in the layout the dense modulus pass reads: a_k^T[v][u] = sqrt(max(d_k[u][v], 0)).
 __global__ void __launch_bounds__(256) k_tc_amp(const float* __restrict__ d, float* __restrict__ amp_t, int m,
                                                 size_t n) {
   const size_t mm = (size_t)m * m;
@@ -479,6 +933,31 @@ __global__ void __launch_bounds__(256) k_tc_amp(const float* __restrict__ d, flo
     const size_t k = i / mm;
     const int p = (int)(i % mm), v = p / m, u = p % m;
     amp_t[i] = sqrtf(fmaxf(d[k * mm + (size_t)u * m + v], 0.f));
+  }
+}
+
+// ... and in the layout the radix-16 modulus pass reads (m = 256): a_k with rows
+// and columns digit-swapped.  One block per row, permuted in shared memory as in
+// k_tc_rows16 so that reads and writes are coalesced.
+__global__ void __launch_bounds__(256) k_tc_amp16(const float* __restrict__ d, float* __restrict__ amp_s,
+                                                  int n_pos) {
+  constexpr int m = 256, R = kR16Rows;
+  __shared__ float sh[R][m + m / 16];
+  const int c = threadIdx.x;
+  const int pc = r16_perm(c);
+  for (int row0 = blockIdx.x * R; row0 < n_pos * m; row0 += gridDim.x * R) {
+    float v[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = d[(size_t)(row0 + i) * m + c];
+#pragma unroll
+    for (int i = 0; i < R; ++i) sh[i][pc + (pc >> 4)] = sqrtf(fmaxf(v[i], 0.f));
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int row = row0 + i, k = row / m, r = row % m;
+      amp_s[((size_t)k * m + r16_perm(r)) * m + c] = sh[i][c + (c >> 4)];
+    }
+    __syncthreads();
   }
 }
 
@@ -619,6 +1098,84 @@ cudaError_t get_tables(int m, const TcTables** out) {
   return cudaSuccess;
 }
 
+// The radix-16 pass: the 32 x 32 real matrices of x -> x W16 and x -> x conj(W16)
+// (K-major, high and low parts), their tensor maps (one 32 x 32 box), and the
+// twiddles W_256^j in constant memory; per device.
+struct TcTables16 {
+  uint16_t* d = nullptr;  // [4][32][32]: fwd hi, fwd lo, inv hi, inv lo
+  CUtensorMap map[4];
+};
+TcTables16 g_tables16[64];
+
+cudaError_t get_tables16(const TcTables16** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  TcTables16& t = g_tables16[dev];
+  {
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    if (t.d) {
+      *out = &t;
+      return cudaSuccess;
+    }
+  }
+  constexpr int K = 32, per = K * K;
+  uint16_t h[4 * per];
+  memset(h, 0, sizeof(h));
+  for (int inv = 0; inv < 2; ++inv) {
+    uint16_t* th = h + (2 * inv) * per;
+    uint16_t* tl = th + per;
+    for (int v = 0; v < 16; ++v)
+      for (int c = 0; c < 16; ++c) {
+        const int t_ = (c * v) % 16;
+        double gr = cos(2.0 * M_PI * t_ / 16), gi = -sin(2.0 * M_PI * t_ / 16);
+        if (fabs(gr) < 1e-15) gr = 0.0;
+        if (fabs(gi) < 1e-15) gi = 0.0;
+        if (inv) gi = -gi;
+        const double val[4] = {gr, -gi, gi, gr};
+        const int idx[4] = {(2 * v) * K + 2 * c, (2 * v) * K + 2 * c + 1, (2 * v + 1) * K + 2 * c,
+                            (2 * v + 1) * K + 2 * c + 1};
+        for (int j = 0; j < 4; ++j) {
+          const uint16_t hv = host_bf16(val[j]);
+          th[idx[j]] = hv;
+          tl[idx[j]] = host_bf16(val[j] - host_bf16_value(hv));
+        }
+      }
+  }
+  float2 tw[256];
+  for (int j = 0; j < 256; ++j) tw[j] = make_float2((float)cos(2.0 * M_PI * j / 256), (float)-sin(2.0 * M_PI * j / 256));
+  uint16_t* d = nullptr;
+  e = cudaMalloc(&d, sizeof(h));
+  if (e == cudaSuccess) e = cudaMemcpy(d, h, sizeof(h), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tw256, tw, sizeof(tw));
+  TcTables16 nt;
+  for (int j = 0; e == cudaSuccess && j < 4; ++j) e = make_map(&nt.map[j], d + j * per, K, K, 32);
+  if (e != cudaSuccess) {
+    if (d) cudaFree(d);
+    return e;
+  }
+  std::lock_guard<std::mutex> lk(g_tc_mu);
+  if (t.d) {
+    cudaFree(d);
+  } else {
+    nt.d = d;
+    t = nt;
+  }
+  *out = &t;
+  return cudaSuccess;
+}
+
+template <int EPI>
+cudaError_t launch_pass16(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
+                          int rows, int sms, TcPassArgs a, int inverse, cudaStream_t s) {
+  a.tiles_n = 1;
+  a.m_tiles = rows / kBM;  // blocks of 128 rows
+  const int grid = a.m_tiles < sms ? a.m_tiles : sms;
+  k_tc_fft16<EPI><<<grid, kTcThreads, kR16Smem, s>>>(ah, al, bh, bl, a, inverse);
+  return cudaGetLastError();
+}
+
 template <int EPI>
 cudaError_t launch_pass(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
                         int rows, int sms, TcPassArgs a, cudaStream_t s) {
@@ -641,6 +1198,15 @@ cudaError_t set_tc_attrs() {
   if ((e = cudaFuncSetAttribute(k_tc_dft<kEpiF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem)) !=
       cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(k_tc_fft16<kEpiSplitT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kR16Smem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_tc_fft16<kEpiModulus>, cudaFuncAttributeMaxDynamicSharedMemorySize, kR16Smem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_tc_fft16<kEpiF32T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kR16Smem)) !=
+      cudaSuccess)
+    return e;
   return cudaFuncSetAttribute(k_tc_dft<kEpiF32T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
 }
 
@@ -656,11 +1222,22 @@ struct TcWork {
   uint32_t* buf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [ping-pong][hi, lo]: bf16 pairs [cap m][m]
   CUtensorMap amap[2][2];   // the two buffers as A operands
   const TcTables* tables = nullptr;
+  const TcTables16* tables16 = nullptr;  // the radix-16 pass (m = 256)
   int* d_err = nullptr;
   int sms = 0;              // persistent grid: one CTA per SM
 };
 
 bool tc_supported(int m) { return m == 128 || m == 256; }
+
+// m = 256 runs the radix-16 pass unless EMG_TC_RADIX16=0 (read once per process,
+// so that every work area and the transposed amplitudes agree on the layout).
+bool tc_radix16(int m) {
+  static const bool on = [] {
+    const char* v = getenv("EMG_TC_RADIX16");
+    return !(v && v[0] == '0');
+  }();
+  return m == 256 && on;
+}
 
 cudaError_t tc_work_create(TcWork** out, int m, int cap) {
   *out = nullptr;
@@ -681,6 +1258,7 @@ cudaError_t tc_work_create(TcWork** out, int m, int cap) {
   }
   const size_t pairs = (size_t)cap * m * m;
   cudaError_t e = get_tables(m, &w->tables);
+  if (e == cudaSuccess && tc_radix16(m)) e = get_tables16(&w->tables16);
   for (int i = 0; e == cudaSuccess && i < 2; ++i)
     for (int j = 0; e == cudaSuccess && j < 2; ++j) {
       e = cudaMalloc(&w->buf[i][j], pairs * sizeof(uint32_t));
@@ -707,15 +1285,39 @@ void tc_work_destroy(TcWork* w) {
 
 int* tc_error_flag(TcWork* w) { return w->d_err; }
 
-int tc_tiles_per_position(int m) { return (m / kBM) * (2 * m / kBN) * kEpiWarps; }  // per epilogue warp
+int tc_tiles_per_position(int m) {  // partial sums per position: one per output tile and epilogue warp
+  return tc_radix16(m) ? (m / kBM) * kEpiWarps : (m / kBM) * (2 * m / kBN) * kEpiWarps;
+}
 
 cudaError_t tc_dft2(TcWork* w, const float2* in, float2* out, int count, int inverse, cudaStream_t s) {
   if (count < 1 || count > w->cap) return cudaErrorInvalidValue;
   const int m = w->m, rows = count * m;
   const size_t n = (size_t)count * m * m;
-  k_tc_split<<<grid_for(n), 256, 0, s>>>(in, w->buf[0][0], w->buf[0][1], n);
+  const bool r16 = tc_radix16(m);
+  if (r16)
+    k_tc_rows16<<<rows / kR16Rows, 256, 0, s>>>(in, nullptr, nullptr, nullptr, nullptr, 0, 0, count, w->buf[0][0],
+                                               w->buf[0][1]);
+  else
+    k_tc_split<<<grid_for(n), 256, 0, s>>>(in, w->buf[0][0], w->buf[0][1], n);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (r16) {
+    const CUtensorMap* B = &w->tables16->map[inverse ? 2 : 0];
+    TcPassArgs a{};
+    a.m = m;
+    a.err = w->d_err;
+    a.out_hi = w->buf[1][0];
+    a.out_lo = w->buf[1][1];
+    a.scale = 1.f;
+    a.rows16 = 0;  // [kc][r]: rows natural, elements digit-swapped
+    if ((e = launch_pass16<kEpiSplitT>(w->amap[0][0], w->amap[0][1], B[0], B[1], rows, w->sms, a, inverse, s)) !=
+        cudaSuccess)
+      return e;
+    a.out_hi = a.out_lo = nullptr;
+    a.out_f32 = out;
+    a.scale = inverse ? 1.f / (float)(m * m) : 1.f;
+    return launch_pass16<kEpiF32T>(w->amap[1][0], w->amap[1][1], B[0], B[1], rows, w->sms, a, inverse, s);
+  }
   const CUtensorMap* B = &w->tables->map[inverse ? 2 : 0];
   TcPassArgs a{};
   a.m = m;
@@ -734,10 +1336,55 @@ cudaError_t tc_exit_waves(TcWork* w, const TcStepArgs& t, cudaStream_t s) {
   if (t.b < 1 || t.b > w->cap) return cudaErrorInvalidValue;
   const int m = w->m, rows = t.b * m;
   const size_t n = (size_t)t.b * m * m;
-  k_tc_psi<<<grid_for(n), 256, 0, s>>>(t.object, t.probe, t.pos, t.order, t.n_rows, t.n_cols, m, t.b, w->buf[0][0],
-                                       w->buf[0][1]);
+  const bool r16 = tc_radix16(m);
+  if (r16)
+    k_tc_rows16<<<rows / kR16Rows, 256, 0, s>>>(nullptr, t.object, t.probe, t.pos, t.order, t.n_rows, t.n_cols,
+                                                t.b, w->buf[0][0], w->buf[0][1]);
+  else
+    k_tc_psi<<<grid_for(n), 256, 0, s>>>(t.object, t.probe, t.pos, t.order, t.n_rows, t.n_cols, m, t.b,
+                                         w->buf[0][0], w->buf[0][1]);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (r16) {
+    // The same four passes, each a radix-16 pass with transposed outputs.  Tile
+    // layouts (rows x elements; "swapped" = stored at r16_perm of the index):
+    // psi [r][c] both swapped -> [kc][r] both swapped -> (modulus) [kr][kc] both
+    // swapped -> [c][kr] elements swapped -> R [r][c] natural.
+    const CUtensorMap* F = &w->tables16->map[0];
+    const CUtensorMap* G = &w->tables16->map[2];
+    TcPassArgs a{};
+    a.m = m;
+    a.err = w->d_err;
+    a.scale = 1.f;
+    a.out_hi = w->buf[1][0];
+    a.out_lo = w->buf[1][1];
+    a.rows16 = 1;
+    if ((e = launch_pass16<kEpiSplitT>(w->amap[0][0], w->amap[0][1], F[0], F[1], rows, w->sms, a, 0, s)) !=
+        cudaSuccess)
+      return e;
+    a.out_hi = w->buf[0][0];
+    a.out_lo = w->buf[0][1];
+    a.amp_t = t.amp_t;
+    a.order = t.order;
+    a.partial = t.partial;
+    a.scale = 1.f / (float)(m * m);
+    if ((e = launch_pass16<kEpiModulus>(w->amap[1][0], w->amap[1][1], F[0], F[1], rows, w->sms, a, 0, s)) !=
+        cudaSuccess)
+      return e;
+    a.amp_t = nullptr;
+    a.order = nullptr;
+    a.partial = nullptr;
+    a.scale = 1.f;
+    a.out_hi = w->buf[1][0];
+    a.out_lo = w->buf[1][1];
+    a.rows16 = 0;
+    if ((e = launch_pass16<kEpiSplitT>(w->amap[0][0], w->amap[0][1], G[0], G[1], rows, w->sms, a, 1, s)) !=
+        cudaSuccess)
+      return e;
+    a.out_hi = a.out_lo = nullptr;
+    a.out_f32 = t.R;
+    return launch_pass16<kEpiF32T>(w->amap[1][0], w->amap[1][1], G[0], G[1], rows, w->sms, a, 1, s);
+  }
   const CUtensorMap* F = &w->tables->map[0];
   const CUtensorMap* G = &w->tables->map[2];
   TcPassArgs a{};
@@ -776,7 +1423,12 @@ cudaError_t launch_wait_selftest(int* err, cudaStream_t s) {
 
 cudaError_t launch_tc_amp(const float* d, float* amp_t, int m, int n_pos, cudaStream_t s) {
   const size_t n = (size_t)n_pos * m * m;
-  k_tc_amp<<<grid_for(n), 256, 0, s>>>(d, amp_t, m, n);
+  if (tc_radix16(m)) {
+    const int groups = n_pos * m / kR16Rows, grid = groups < 65536 ? groups : 65536;
+    k_tc_amp16<<<grid, 256, 0, s>>>(d, amp_t, n_pos);
+  } else {
+    k_tc_amp<<<grid_for(n), 256, 0, s>>>(d, amp_t, m, n);
+  }
   return cudaGetLastError();
 }
 

@@ -126,6 +126,12 @@ def test_context_free_calls_validate_arguments(lib):
     assert lib.emg_illuminated_region(None, 4, 0x10, 1, 8, 8, 0.1, 0x20, None) == emg.EMG_EINVAL
     assert lib.emg_illuminated_region(0x10, 4, 0x20, 1, 8, 8, float("nan"), 0x30, None) == emg.EMG_EINVAL
     assert lib.emg_illuminated_region(0x10, 4, 0x20, 0, 8, 8, 0.1, 0x30, None) == emg.EMG_EINVAL
+    form = ctypes.c_int32(-1)
+    assert lib.emg_dft_bf16x3_form(256, None) == emg.EMG_EINVAL
+    assert lib.emg_dft_bf16x3_form(64, ctypes.byref(form)) == emg.EMG_ENOTSUP
+    assert lib.emg_dft_bf16x3_form(128, ctypes.byref(form)) == emg.EMG_OK and form.value == 0
+    assert lib.emg_dft_bf16x3_form(256, ctypes.byref(form)) == emg.EMG_OK
+    assert form.value == (0 if os.environ.get("EMG_TC_RADIX16", "").startswith("0") else 1)
     lib.emg_destroy(None)  # no-op
 
 
