@@ -141,6 +141,60 @@ __device__ __forceinline__ float2 geometric_mean_aligned_fast(float2 x, float2 x
   return y;
 }
 
+// c + a b, c - a b and c + conj(a) b as chains of two fused multiply-adds per part.
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float2 cfnma(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float2 cfma_conj(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+
+// y with y^2 = x * xp and Re(y conj(x)) >= 0 (Eq. geomean), branch-free, in
+// the half-angle form of geometric_mean_aligned_fast with s' = 2 s, so that
+// t = sqrt(s) = s' r / sqrt(2) and v h = v r / sqrt(2) for r = 1 / sqrt(s').
+// A floor of 1e-37 under both square roots gives y = 0 for w = 0 without a
+// branch; it changes no result for |w|^2 above about 1e-29.  The sign flip
+// is applied to the sign bit when Re(y conj(x)) < 0.
+__device__ __forceinline__ float2 geomean_aligned_root(float2 x, float2 xp) {
+  const float2 w = cmul(x, xp);
+  const float n = fmaf(w.x, w.x, w.y * w.y);
+  const float mag = n * rsqrtf(n + 1e-37f);
+  const float s2 = fabsf(w.x) + mag;
+  const float rr = rsqrtf(s2 + 1e-37f) * 0.70710678118654752f;
+  const float t = s2 * rr, vh = w.y * rr;
+  const float yx = w.x >= 0.f ? t : vh, yy = w.x >= 0.f ? vh : t;
+  const unsigned sbit = fmaf(yx, x.x, yy * x.y) < 0.f ? 0x80000000u : 0u;
+  return make_float2(__uint_as_float(__float_as_uint(yx) ^ sbit), __uint_as_float(__float_as_uint(yy) ^ sbit));
+}
+
+// a5 (finest level) + a6 + a7 at one pixel: with MG the fine MAGPIE step from
+// the prolonged coarse correction pro, z^+ = zp + G_0 (R - Q zp) with
+// zp = z_k + pro, else z^+ = z_k + G_0 (R - Q z_k); Q^+ = Q + conj(z_k)(R - Q z_k)/mu_k;
+// with JOINT their aligned geometric means with z_k and Q (Eq. geomean).
+template <bool MG, bool JOINT>
+__device__ __forceinline__ void update_pixel(float2 zk, float2 q, float2 g0, float2 R, float2 pro, float inv_mu,
+                                             float2& zn, float2& qn) {
+  const float2 res = cfnma(q, zk, R);
+  float2 zplus;
+  if constexpr (MG) {
+    const float2 zp = cadd(zk, pro);
+    zplus = cfma(g0, cfnma(q, zp, R), zp);
+  } else {
+    zplus = cfma(g0, res, zk);
+  }
+  const float2 qplus = cfma_conj(zk, cscale(res, inv_mu), q);
+  if constexpr (JOINT) {
+    zn = geomean_aligned_root(zk, zplus);
+    qn = geomean_aligned_root(q, qplus);
+  } else {
+    zn = zplus;
+    qn = qplus;
+  }
+}
+
 // Atomic object scatter of one patch pixel (EMG_SCATTER_ATOMIC): weighted mean
 // (combine 0) adds w z~ and w, the summed corrections (combine 1) add z~ - z_k.
 __device__ __forceinline__ void scatter_atomic(float2* num, float* den, int combine, int n_rows, int n_cols, int gr,
@@ -1227,54 +1281,66 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
     __syncthreads();
   }
 
-  // a5 (finest level) + a6 + a7; the level-0 gain conj(Q)/(u_0 + |Q|^2) is formed here
+  // a5 (finest level) + a6 + a7; the level-0 gain G_0 = conj(Q)/(u_0 + |Q|^2)
+  // comes from the probe prep of this minibatch
   const float inv_mu = mu > 0.f ? 1.f / mu : 0.f;
   float2* zt = a.zt + (size_t)kb * M * M;
   float2* qt = a.qt + (size_t)kb * M * M;
   const float2* Z1 = Zl[1];
+  const float2* G0 = a.lv.G[0];
   float acc_after = 0.f;
-  // Groups of UG pixels: the probe loads of a group are issued together, and
-  // the loop body stays small enough for the instruction cache.
+  // Groups of UG pixels: the probe and gain loads of a group are issued
+  // together, and the loop body stays small enough for the instruction cache.
   constexpr int UG0 = EMG_UPDATE_GROUP < PER ? EMG_UPDATE_GROUP : PER;
   constexpr int UG = PER % UG0 == 0 ? UG0 : 1;
   // The common case (multigrid, joint step, ordered combine, no verify) runs a
   // loop without the mode branches over pairs of adjacent pixels, with 16-byte
-  // probe loads and patch stores; the arithmetic per pixel is the same.
+  // probe and gain loads and patch stores, and the prolongation's loads shared
+  // by the pair; the arithmetic per pixel is the same as in the general loop.
   constexpr int UGP = UG >= 2 && PER % 2 == 0 ? UG / 2 : 0;
   const bool pairs = UGP > 0 && a.levels > 1 && a.joint && !a.s_num && !a.verify && slot_ok &&
-                     ((reinterpret_cast<uintptr_t>(a.probe) | reinterpret_cast<uintptr_t>(zt) |
-                       reinterpret_cast<uintptr_t>(qt)) & 15) == 0;
+                     ((reinterpret_cast<uintptr_t>(a.probe) | reinterpret_cast<uintptr_t>(G0) |
+                       reinterpret_cast<uintptr_t>(zt) | reinterpret_cast<uintptr_t>(qt)) & 15) == 0;
   if constexpr (UGP > 0) {
     if (pairs) {
       constexpr int PP = PER / 2;
+      constexpr int SL1 = M / 2 + 1, WC1 = M / 2;
 #pragma unroll 1
       for (int t0 = 0; t0 < PP; t0 += UGP) {
-        float4 qv[UGP];
+        float4 qv[UGP], gv[UGP];
 #pragma unroll
-        for (int u = 0; u < UGP; ++u)
-          qv[u] = __ldg(reinterpret_cast<const float4*>(a.probe + row0 * M + 2 * (tid + (t0 + u) * NT)));
+        for (int u = 0; u < UGP; ++u) {
+          const int off = row0 * M + 2 * (tid + (t0 + u) * NT);
+          qv[u] = __ldg(reinterpret_cast<const float4*>(a.probe + off));
+          gv[u] = __ldcg(reinterpret_cast<const float4*>(G0 + off));
+        }
 #pragma unroll
         for (int u = 0; u < UGP; ++u) {
           const int p0 = 2 * (tid + (t0 + u) * NT);
           const int lr = p0 / M, c0 = p0 % M, r = row0 + lr;
           const float4 zk2 = *reinterpret_cast<const float4*>(zbuf + p0);
+          // coarse-level correction at both pixels: the rows and the centre column are shared
+          float2 pro[2];
+          {
+            const int i = lr >> 1, j = c0 >> 1;
+            const float2* y0 = Z1 + i * SL1;
+            const float2 v = y0[j];
+            if (a.prolong == 0) {
+              pro[0] = pro[1] = v;
+            } else {
+              const float2* y1 = Z1 + ((lr & 1) ? i + 1 : i - 1) * SL1;
+              const int jm = max(j - 1, 0), jp = min(j + 1, WC1 - 1);
+              pro[0] = lerp4<float2>(v, y1[j], y0[jm], y1[jm]);
+              pro[1] = lerp4<float2>(v, y1[j], y0[jp], y1[jp]);
+            }
+          }
           float2 zo[2], qo[2];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const int c = c0 + h;
             const float2 zk = h ? make_float2(zk2.z, zk2.w) : make_float2(zk2.x, zk2.y);
             const float2 q = h ? make_float2(qv[u].z, qv[u].w) : make_float2(qv[u].x, qv[u].y);
-            const float2 R = rowbuf[lr * SR + c];
-            const float2 res = csub(R, cmul(q, zk));
-            const float a2 = cabs2(q);
-            const float den = fmaf(a.alpha, MQ - a2, a2);
-            const float2 g0 = den != 0.f ? cscale(cconj(q), __frcp_rn(den)) : czero();
-            const float2 pro = prolong_halo<float2>(Z1, M / 2 + 1, M / 2, lr, c, a.prolong);
-            const float2 zp = cadd(zk, pro);
-            const float2 zplus = cadd(zp, cmul(g0, csub(R, cmul(q, zp))));
-            const float2 qplus = cadd(q, cscale(cconjmul(zk, res), inv_mu));
-            zo[h] = geometric_mean_aligned_fast(zk, zplus);
-            qo[h] = geometric_mean_aligned_fast(q, qplus);
+            const float2 g0 = h ? make_float2(gv[u].z, gv[u].w) : make_float2(gv[u].x, gv[u].y);
+            update_pixel<true, true>(zk, q, g0, rowbuf[lr * SR + c0 + h], pro[h], inv_mu, zo[h], qo[h]);
           }
           *reinterpret_cast<float4*>(zt + r * M + c0) = make_float4(zo[0].x, zo[0].y, zo[1].x, zo[1].y);
           *reinterpret_cast<float4*>(qt + r * M + c0) = make_float4(qo[0].x, qo[0].y, qo[1].x, qo[1].y);
@@ -1284,9 +1350,12 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
   }
 #pragma unroll 1
   for (int t0 = 0; t0 < (pairs ? 0 : PER); t0 += UG) {
-  float2 qv[UG];
+  float2 qv[UG], gv[UG];
 #pragma unroll
-  for (int u = 0; u < UG; ++u) qv[u] = __ldg(a.probe + row0 * M + tid + (t0 + u) * NT);
+  for (int u = 0; u < UG; ++u) {
+    qv[u] = __ldg(a.probe + row0 * M + tid + (t0 + u) * NT);
+    gv[u] = __ldcg(G0 + row0 * M + tid + (t0 + u) * NT);
+  }
 #pragma unroll
   for (int u = 0; u < UG; ++u) {
     const int t = t0 + u;
@@ -1295,29 +1364,21 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
     const float2 zk = zbuf[p];
     const float2 q = qv[u];
     const float2 R = rowbuf[lr * SR + c];
-    const float2 res = csub(R, cmul(q, zk));
-    const float a2 = cabs2(q);
-    const float den = fmaf(a.alpha, MQ - a2, a2);
-    const float2 g0 = den != 0.f ? cscale(cconj(q), __frcp_rn(den)) : czero();
-    float2 zplus;
-    if (a.levels == 1) {
-      zplus = cadd(zk, cmul(g0, res));
-    } else {
-      const float2 pro = prolong_halo<float2>(Z1, M / 2 + 1, M / 2, lr, c, a.prolong);
-      const float2 zp = cadd(zk, pro);
-      zplus = cadd(zp, cmul(g0, csub(R, cmul(q, zp))));
-    }
-    const float2 qplus = cadd(q, cscale(cconjmul(zk, res), inv_mu));
+    const float2 pro = a.levels == 1 ? czero() : prolong_halo<float2>(Z1, M / 2 + 1, M / 2, lr, c, a.prolong);
     float2 zn, qn;
-    if (a.joint) {
-      zn = geometric_mean_aligned_fast(zk, zplus);
-      qn = geometric_mean_aligned_fast(q, qplus);
+    if (a.levels == 1) {
+      if (a.joint)
+        update_pixel<false, true>(zk, q, gv[u], R, pro, inv_mu, zn, qn);
+      else
+        update_pixel<false, false>(zk, q, gv[u], R, pro, inv_mu, zn, qn);
     } else {
-      zn = zplus;
-      qn = qplus;
+      if (a.joint)
+        update_pixel<true, true>(zk, q, gv[u], R, pro, inv_mu, zn, qn);
+      else
+        update_pixel<true, false>(zk, q, gv[u], R, pro, inv_mu, zn, qn);
     }
     if (a.s_num)
-      scatter_atomic(a.s_num, a.s_den, a.combine, a.n_rows, a.n_cols, o_r + r, o_c + c, zn, zk, fmaf(a.w_eps, MQ, a2));
+      scatter_atomic(a.s_num, a.s_den, a.combine, a.n_rows, a.n_cols, o_r + r, o_c + c, zn, zk, fmaf(a.w_eps, MQ, cabs2(q)));
     else if (slot_ok)
       zt[r * M + c] = zn;
     if (slot_ok) qt[r * M + c] = qn;
