@@ -913,6 +913,18 @@ __device__ __forceinline__ T prolong_halo(const T* y, int sl, int wc, int lr, in
   return lerp4<T>(v, y[i2 * sl + j], y[i * sl + j2], y[i2 * sl + j2]);
 }
 
+// Stores coarse value v of local row i, column j (a slab of hl rows, row stride
+// sl, y at my first row) where the halo rows of the prolongation read it: my
+// first row into the upper neighbour's bottom halo row (my own top halo row
+// at the patch's top edge), my last row into the lower neighbour's top halo
+// row (my own bottom halo row at the bottom edge).  A cluster barrier makes
+// the rows visible before they are read.
+template <int C, typename T>
+__device__ __forceinline__ void push_halo(cg::cluster_group& cl, int rank, T* y, int sl, int hl, int i, int j, T v) {
+  if (i == 0) *(rank > 0 ? cl.map_shared_rank(y, rank - 1) + hl * sl + j : y - sl + j) = v;
+  if (i == hl - 1) *(rank < C - 1 ? cl.map_shared_rank(y, rank + 1) - sl + j : y + hl * sl + j) = v;
+}
+
 // RIN = true: the revised exit waves R_k and the misfit partials come from the
 // tensor-core DFT pair (a2-a4 done elsewhere); the kernel gathers z_k and runs
 // a5-a7 only.
@@ -1160,9 +1172,9 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
           const float2 wz = __ldcg(reinterpret_cast<const float2*>(Wz + r * M + c));
           const float4 wr = __ldcg(reinterpret_cast<const float4*>(WR + r * M + c));
           zs = cadd(zs, cscale(zbuf[lr * M + c], wz.x));
-          rs = cadd(rs, cmul(make_float2(wr.x, wr.y), rowbuf[lr * SR + c]));
+          rs = cfma(make_float2(wr.x, wr.y), rowbuf[lr * SR + c], rs);
           zs = cadd(zs, cscale(zbuf[lr * M + c + 1], wz.y));
-          rs = cadd(rs, cmul(make_float2(wr.z, wr.w), rowbuf[lr * SR + c + 1]));
+          rs = cfma(make_float2(wr.z, wr.w), rowbuf[lr * SR + c + 1], rs);
         }
         Z1w[i * sc + j] = cscale(zs, 0.25f);
         R1w[i * sc + j] = cscale(rs, 0.25f);
@@ -1184,19 +1196,18 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
           for (int dy = 0; dy < 2; ++dy) {
             const int lr = 2 * i + dy, c = 2 * j;
             zs = cadd(zs, cscale(Zf[lr * sf + c], pf_wz1[t][dy].x));
-            rs = cadd(rs, cmul(make_float2(pf_wr1[t][dy].x, pf_wr1[t][dy].y), Rf[lr * sf + c]));
+            rs = cfma(make_float2(pf_wr1[t][dy].x, pf_wr1[t][dy].y), Rf[lr * sf + c], rs);
             zs = cadd(zs, cscale(Zf[lr * sf + c + 1], pf_wz1[t][dy].y));
-            rs = cadd(rs, cmul(make_float2(pf_wr1[t][dy].z, pf_wr1[t][dy].w), Rf[lr * sf + c + 1]));
+            rs = cfma(make_float2(pf_wr1[t][dy].z, pf_wr1[t][dy].w), Rf[lr * sf + c + 1], rs);
           }
           const float2 z2 = cscale(zs, 0.25f), r2 = cscale(rs, 0.25f);
           // coarsest level 2: correction c = G (R - Q z), stored over z
-          Zc[i * sc + j] = cmul(pf_g2[t], csub(r2, cmul(pf_q2[t], z2)));
+          const float2 cc = cmul(pf_g2[t], cfnma(pf_q2[t], z2, r2));
+          Zc[i * sc + j] = cc;
+          if (halo) push_halo<C>(cl, rank, Zc, sc, hc2, i, j, cc);
         }
       }
-      if (halo) {
-        cl.sync();
-        fill_halo(2);
-      }
+      if (halo) cl.sync();  // the pushed halo rows of level 2 are in place
       __syncthreads();
       {  // back up to level 1
         constexpr int sl = wc1 + 1, sc = wc2 + 1;
@@ -1208,7 +1219,9 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
           const int p = tid + t * NT, i = p / wc1, j = p % wc1;
           const float2 pro = prolong_halo<float2>(Zc, sc, wc2, i, j, a.prolong);
           const float2 zp = cadd(Zw[i * sl + j], pro);
-          Zw[i * sl + j] = cadd(pro, cmul(pf_g1[t], csub(Rw[i * sl + j], cmul(pf_q1[t], zp))));
+          const float2 cc = cfma(pf_g1[t], cfnma(pf_q1[t], zp, Rw[i * sl + j]), pro);
+          Zw[i * sl + j] = cc;
+          if (halo) push_halo<C>(cl, rank, Zw, sl, hc1, i, j, cc);
         }
       }
     } else {
@@ -1276,7 +1289,7 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
     }  // generic levels
     if (halo) {
       cl.sync();
-      fill_halo(1);
+      if (!l3) fill_halo(1);  // three levels: the halo rows were pushed
     }
     __syncthreads();
   }
@@ -1389,11 +1402,14 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
     const double part = 0.5 * block_sum_f<NT>(acc_after, redf, redd);
     if (tid == 0) cluster_publish<C>(cl, rank, xd2, part);
   }
-  // Neighbours may still read my coarse rows: no CTA leaves before all arrive.
-  // The verify mode also publishes xd2, which needs the release / acquire pair.
+  // With halo rows read from the neighbours (bilinear prolongation, other
+  // than three levels) a neighbour may still read my coarse rows: no CTA leaves
+  // before all arrive.  The verify mode also publishes xd2, which needs the
+  // release / acquire pair.  Otherwise no CTA touches another's shared memory
+  // after the last cluster barrier, and each may leave when done.
   if (a.verify) {
     cl.sync();
-  } else {
+  } else if (halo && !l3 && a.levels > 1) {
     cluster_arrive_relaxed();
     cluster_wait();
   }
