@@ -582,8 +582,8 @@ emg_status enqueue_minibatch(emg_ctx* c, const int32_t* d_idx, int b, double* d_
   aa.mu = mu_all;
   aa.wq = c->d_wq;
   aa.mq_next = c->d_mq + ((seq + 1) & 1);
-  aa.tiles_x = (c->n_cols + emg::kApplyTile - 1) / emg::kApplyTile;
-  aa.tiles_y = (c->n_rows + emg::kApplyTile - 1) / emg::kApplyTile;
+  aa.tiles_x = emg::apply_tiles_x(c->n_cols);
+  aa.tiles_y = emg::apply_tiles_y(c->n_rows);
   aa.s_num = atomic ? c->d_snum : nullptr;
   aa.s_den = atomic ? c->d_sden : nullptr;
   {

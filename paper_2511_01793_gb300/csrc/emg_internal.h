@@ -162,9 +162,22 @@ cudaError_t launch_batch_orders(const int32_t* const* src, int32_t* const* dst, 
                                 const int* epoch, cudaStream_t s);
 cudaError_t launch_epoch_advance(int* epoch, cudaStream_t s);
 
+// Combine object tiles: kApplyTile rows x kApplyTileW columns, kApplyPx pixels
+// per thread (the gradient sums use kApplyTile^2 tiles, one pixel per thread).
+#ifndef EMG_APPLY_PX
+#define EMG_APPLY_PX 2
+#endif
+#ifndef EMG_APPLY_PROBE_PX
+#define EMG_APPLY_PROBE_PX 2
+#endif
 constexpr int kApplyTile = 16;
-constexpr int kApplyThreads = 256;      // one object pixel per thread
-constexpr int kApplyProbeGroups = 8;    // probe blocks: 32 pixels x 8 position groups
+constexpr int kApplyPx = EMG_APPLY_PX;
+constexpr int kApplyTileW = kApplyTile * kApplyPx;
+constexpr int kApplyThreads = 256;
+constexpr int kApplyProbeGroups = 8;   // probe blocks: kApplyProbePx pixels x 8 position groups
+constexpr int kApplyProbePx = 32 * EMG_APPLY_PROBE_PX;
+inline int apply_tiles_x(int n_cols) { return (n_cols + kApplyTileW - 1) / kApplyTileW; }
+inline int apply_tiles_y(int n_rows) { return (n_rows + kApplyTile - 1) / kApplyTile; }
 
 cudaError_t upload_twiddles();
 cudaError_t launch_amp_prep(const float* d, float* amp, int m, int n_pos, cudaStream_t s);

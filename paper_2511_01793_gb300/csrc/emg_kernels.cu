@@ -1704,16 +1704,24 @@ __global__ void __launch_bounds__(kApplyThreads) k_grad_reduce(const GradReduceA
 }
 
 // ---------------------------------------------------------------------------
-// a8 + a9: deterministic combine.  Blocks [0, tiles) own 16 x 16 object tiles
-// (one pixel per thread); the remaining blocks own 32 probe pixels each, with
-// 8 thread groups summing disjoint position subsets that are then added in a
-// fixed order.  The new probe's max|Q|^2 goes to a.mq_next for the next prep.
-__global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
+// a8 + a9: deterministic combine.  Blocks [0, tiles) own object tiles of
+// kApplyTile x kApplyTileW pixels (kApplyPx pixels per thread, kApplyTile
+// apart in the row); the remaining blocks own kApplyProbePx probe pixels each
+// (kApplyProbePx / 32 per lane), with 8 thread groups summing disjoint
+// position subsets that are then added in a fixed order.  Each thread issues
+// the loads of all its pixels together, and the grid of the bench-sized
+// object and probe is resident at once after the step.  The new probe's
+// max|Q|^2 goes to a.mq_next for the next prep.
+#ifndef EMG_APPLY_MIN_BLOCKS
+#define EMG_APPLY_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(kApplyThreads, EMG_APPLY_MIN_BLOCKS) k_apply(const ApplyArgs a) {
+  constexpr int PX = kApplyPx, PP = kApplyProbePx / 32;
   extern __shared__ int list[];  // [b][3] = (kb, row, col) of patches overlapping the tile
   __shared__ int warp_count[kApplyThreads / 32];
   __shared__ int total;
-  __shared__ float2 part_s[kApplyProbeGroups][32];
-  __shared__ int part_n[kApplyProbeGroups][32];
+  __shared__ float2 part_s[kApplyProbeGroups][kApplyProbePx];
+  __shared__ int part_n[kApplyProbeGroups][kApplyProbePx];
   const int tid = threadIdx.x;
   const int n_tiles = a.tiles_x * a.tiles_y;
   const int m = a.m;
@@ -1722,27 +1730,32 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
   if ((int)blockIdx.x < n_tiles && a.s_num) {
     // atomic scatter: the step kernel has accumulated this tile's sums; finalise and reset them
     const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x % a.tiles_x;
-    const int row = ty * kApplyTile + tid / kApplyTile, col = tx * kApplyTile + tid % kApplyTile;
-    if (row >= a.n_rows || col >= a.n_cols) return;
+    const int row = ty * kApplyTile + tid / kApplyTile;
+    if (row >= a.n_rows) return;
     pdl_wait();
-    const size_t gi = (size_t)row * a.n_cols + col;
-    if (a.combine == 0) {
-      const float den = a.s_den[gi];
-      if (den > 0.f) {
-        a.object[gi] = cscale(a.s_num[gi], 1.f / den);
-        a.s_num[gi] = czero();
-        a.s_den[gi] = 0.f;
-      }
-    } else {
-      const float2 dz = a.s_num[gi];
-      if (dz.x != 0.f || dz.y != 0.f) {
-        a.object[gi] = cadd(a.object[gi], dz);
-        a.s_num[gi] = czero();
+#pragma unroll
+    for (int h = 0; h < PX; ++h) {
+      const int col = tx * kApplyTileW + tid % kApplyTile + h * kApplyTile;
+      if (col >= a.n_cols) continue;
+      const size_t gi = (size_t)row * a.n_cols + col;
+      if (a.combine == 0) {
+        const float den = a.s_den[gi];
+        if (den > 0.f) {
+          a.object[gi] = cscale(a.s_num[gi], 1.f / den);
+          a.s_num[gi] = czero();
+          a.s_den[gi] = 0.f;
+        }
+      } else {
+        const float2 dz = a.s_num[gi];
+        if (dz.x != 0.f || dz.y != 0.f) {
+          a.object[gi] = cadd(a.object[gi], dz);
+          a.s_num[gi] = czero();
+        }
       }
     }
   } else if ((int)blockIdx.x < n_tiles) {
     const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x % a.tiles_x;
-    const int r0 = ty * kApplyTile, c0 = tx * kApplyTile;
+    const int r0 = ty * kApplyTile, c0 = tx * kApplyTileW;
     if (tid == 0) total = 0;
     __syncthreads();
     // ordered compaction of the minibatch patches that overlap this tile
@@ -1755,7 +1768,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
         if (!EMG_INB(k, a.n_pos, kBcApplyOrder)) k = 0;
         pr = a.pos[2 * k];
         pc = a.pos[2 * k + 1];
-        hit = pr < r0 + kApplyTile && pr + m > r0 && pc < c0 + kApplyTile && pc + m > c0;
+        hit = pr < r0 + kApplyTile && pr + m > r0 && pc < c0 + kApplyTileW && pc + m > c0;
       }
       const unsigned mask = __ballot_sync(0xffffffffu, hit);
       const int lane = tid & 31, warp = tid >> 5;
@@ -1778,90 +1791,121 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(const ApplyArgs a) {
       __syncthreads();
     }
     const int cnt = total;
-    const int row = r0 + tid / kApplyTile, col = c0 + tid % kApplyTile;
-    if (cnt == 0 || row >= a.n_rows || col >= a.n_cols) return;
+    const int row = r0 + tid / kApplyTile, col0 = c0 + tid % kApplyTile;
+    if (cnt == 0 || row >= a.n_rows || col0 >= a.n_cols) return;
     pdl_wait();  // patches z~_k and weights come from the step and prep kernels
-    float2 num = czero();
-    float den = 0.f;
-    bool covered = false;
-    // patches in minibatch order; loads of four patches are issued together
+    float2 num[PX];
+    float den[PX];
+    bool covered[PX];
+#pragma unroll
+    for (int h = 0; h < PX; ++h) {
+      num[h] = czero();
+      den[h] = 0.f;
+      covered[h] = false;
+    }
+    // patches in minibatch order; loads of four patches at all pixels are issued together
     for (int t0 = 0; t0 < cnt; t0 += 4) {
-      float2 v[4];
-      float w[4];
-      bool in[4];
+      float2 v[PX][4];
+      float w[PX][4];
+      bool in[PX][4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int t = t0 + u;
-        in[u] = false;
+#pragma unroll
+        for (int h = 0; h < PX; ++h) in[h][u] = false;
         if (t < cnt) {
-          const int lr = row - list[3 * t + 1], lc = col - list[3 * t + 2];
-          in[u] = (unsigned)lr < (unsigned)m && (unsigned)lc < (unsigned)m &&
-                  EMG_INB(list[3 * t], a.b, kBcApplyPatch);
-          if (in[u]) {
-            v[u] = a.zt[(size_t)list[3 * t] * mm + lr * m + lc];
-            w[u] = a.combine == 0 ? a.wq[lr * m + lc] : 1.f;
+          const int kb = list[3 * t], lr = row - list[3 * t + 1], lc = col0 - list[3 * t + 2];
+          const bool ok = (unsigned)lr < (unsigned)m && EMG_INB(kb, a.b, kBcApplyPatch);
+          // all pixels from one base address: pixel h is h kApplyTile columns on
+          const float2* zrow = a.zt + (size_t)kb * mm + lr * m + lc;
+          const float* wrow = a.wq + lr * m + lc;
+#pragma unroll
+          for (int h = 0; h < PX; ++h) {
+            in[h][u] = ok && (unsigned)(lc + h * kApplyTile) < (unsigned)m && col0 + h * kApplyTile < a.n_cols;
+            if (in[h][u]) {
+              v[h][u] = zrow[h * kApplyTile];
+              w[h][u] = a.combine == 0 ? wrow[h * kApplyTile] : 1.f;
+            }
           }
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (in[u]) {
-          covered = true;
-          if (a.combine == 0) {
-            num = make_float2(fmaf(w[u], v[u].x, num.x), fmaf(w[u], v[u].y, num.y));
-          } else {
-            num = cadd(num, v[u]);
+      for (int h = 0; h < PX; ++h)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (in[h][u]) {
+            covered[h] = true;
+            if (a.combine == 0) {
+              num[h] = make_float2(fmaf(w[h][u], v[h][u].x, num[h].x), fmaf(w[h][u], v[h][u].y, num[h].y));
+            } else {
+              num[h] = cadd(num[h], v[h][u]);
+            }
+            den[h] += w[h][u];
           }
-          den += w[u];
         }
-      }
     }
-    if (!covered) return;
-    const size_t gi = (size_t)row * a.n_cols + col;
-    if (!EMG_INB(gi, (size_t)a.n_rows * a.n_cols, kBcApplyObject)) return;
-    if (a.combine == 0) {
-      a.object[gi] = safe_cdiv(num, den);
-    } else {
-      const float2 z = a.object[gi];
-      a.object[gi] = cadd(z, csub(num, cscale(z, den)));
+#pragma unroll
+    for (int h = 0; h < PX; ++h) {
+      if (!covered[h]) continue;
+      const size_t gi = (size_t)row * a.n_cols + col0 + h * kApplyTile;
+      if (!EMG_INB(gi, (size_t)a.n_rows * a.n_cols, kBcApplyObject)) continue;
+      if (a.combine == 0) {
+        a.object[gi] = safe_cdiv(num[h], den[h]);
+      } else {
+        const float2 z = a.object[gi];
+        a.object[gi] = cadd(z, csub(num[h], cscale(z, den[h])));
+      }
     }
   } else {
     pdl_wait();  // probes Q~_k come from the step kernel
     const int lane = tid & 31, g = tid >> 5;
-    const int p = (blockIdx.x - n_tiles) * 32 + lane;
-    float2 s = czero();
+    const int p0 = (blockIdx.x - n_tiles) * kApplyProbePx + lane;
+    float2 s[PP];
+#pragma unroll
+    for (int h = 0; h < PP; ++h) s[h] = czero();
     int cnt = 0;
-    if (p < (int)mm) {
+    if (p0 < (int)mm) {
       for (int kb0 = g; kb0 < a.b; kb0 += 4 * kApplyProbeGroups) {
-        float2 v[4];
+        float2 v[PP][4];
         bool ok[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int kb = kb0 + u * kApplyProbeGroups;
           ok[u] = kb < a.b && a.mu[kb] > 0.f;
-          if (ok[u]) v[u] = a.qt[(size_t)kb * mm + p];
+          if (ok[u]) {
+            const float2* qrow = a.qt + (size_t)kb * mm + p0;
+#pragma unroll
+            for (int h = 0; h < PP; ++h)
+              if (p0 + 32 * h < (int)mm) v[h][u] = qrow[32 * h];
+          }
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           if (ok[u]) {
-            s = cadd(s, v[u]);
+#pragma unroll
+            for (int h = 0; h < PP; ++h)
+              if (p0 + 32 * h < (int)mm) s[h] = cadd(s[h], v[h][u]);
             ++cnt;
           }
         }
       }
     }
-    part_s[g][lane] = s;
-    part_n[g][lane] = cnt;
+#pragma unroll
+    for (int h = 0; h < PP; ++h) {
+      part_s[g][lane + 32 * h] = s[h];
+      part_n[g][lane + 32 * h] = cnt;
+    }
     __syncthreads();
-    if (g != 0) return;
+    if (tid >= kApplyProbePx) return;
+    const int p = (blockIdx.x - n_tiles) * kApplyProbePx + tid;
     float a2 = 0.f;
     if (p < (int)mm) {
-      float2 tot = part_s[0][lane];
-      int n = part_n[0][lane];
+      float2 tot = part_s[0][tid];
+      int n = part_n[0][tid];
 #pragma unroll
       for (int i = 1; i < kApplyProbeGroups; ++i) {
-        tot = cadd(tot, part_s[i][lane]);
-        n += part_n[i][lane];
+        tot = cadd(tot, part_s[i][tid]);
+        n += part_n[i][tid];
       }
       float2 q = a.probe[p];
       if (n > 0) {
@@ -2448,7 +2492,7 @@ cudaError_t launch_epoch_advance(int* epoch, cudaStream_t s) {
 
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
   const int n_tiles = a.tiles_x * a.tiles_y;
-  const int n_probe = (a.m * a.m + 31) / 32;
+  const int n_probe = (a.m * a.m + kApplyProbePx - 1) / kApplyProbePx;
   const size_t bytes = (size_t)a.b * 3 * sizeof(int);
   cudaError_t e = launch_pdl(k_apply, dim3(n_tiles + n_probe), dim3(kApplyThreads), bytes, s, a);
   if (e != cudaSuccess) return e;
@@ -2794,8 +2838,8 @@ extern "C" emg_status emg_step_minibatch_noalloc(float* object, int32_t n_rows, 
   aa.mu = sa.mu;
   aa.wq = pa.wq;
   aa.mq_next = d_mq + 1;
-  aa.tiles_x = (n_cols + kApplyTile - 1) / kApplyTile;
-  aa.tiles_y = (n_rows + kApplyTile - 1) / kApplyTile;
+  aa.tiles_x = apply_tiles_x(n_cols);
+  aa.tiles_y = apply_tiles_y(n_rows);
 
   cudaError_t e = launch_prep(pa, s);
   if (e == cudaSuccess) {
