@@ -1715,6 +1715,10 @@ __global__ void __launch_bounds__(kApplyThreads) k_grad_reduce(const GradReduceA
 #ifndef EMG_APPLY_MIN_BLOCKS
 #define EMG_APPLY_MIN_BLOCKS 4
 #endif
+#ifndef EMG_APPLY_CHUNK
+#define EMG_APPLY_CHUNK 4
+#endif
+constexpr int kApplyChunk = EMG_APPLY_CHUNK;  // covering patches whose loads a thread issues together
 __global__ void __launch_bounds__(kApplyThreads, EMG_APPLY_MIN_BLOCKS) k_apply(const ApplyArgs a) {
   constexpr int PX = kApplyPx, PP = kApplyProbePx / 32;
   extern __shared__ int list[];  // [b][3] = (kb, row, col) of patches overlapping the tile
@@ -1803,13 +1807,13 @@ __global__ void __launch_bounds__(kApplyThreads, EMG_APPLY_MIN_BLOCKS) k_apply(c
       den[h] = 0.f;
       covered[h] = false;
     }
-    // patches in minibatch order; loads of four patches at all pixels are issued together
-    for (int t0 = 0; t0 < cnt; t0 += 4) {
-      float2 v[PX][4];
-      float w[PX][4];
-      bool in[PX][4];
+    // patches in minibatch order; loads of kApplyChunk patches at all pixels are issued together
+    for (int t0 = 0; t0 < cnt; t0 += kApplyChunk) {
+      float2 v[PX][kApplyChunk];
+      float w[PX][kApplyChunk];
+      bool in[PX][kApplyChunk];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kApplyChunk; ++u) {
         const int t = t0 + u;
 #pragma unroll
         for (int h = 0; h < PX; ++h) in[h][u] = false;
@@ -1832,7 +1836,7 @@ __global__ void __launch_bounds__(kApplyThreads, EMG_APPLY_MIN_BLOCKS) k_apply(c
 #pragma unroll
       for (int h = 0; h < PX; ++h)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kApplyChunk; ++u) {
           if (in[h][u]) {
             covered[h] = true;
             if (a.combine == 0) {
