@@ -331,25 +331,46 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_amp_gather(const float* _
                                                                  float* __restrict__ amp) {
   constexpr int PL = (M + 31) / 32, RW = kGatherRows;
   static_assert(M % RW == 0, "row groups stay within one position");
-  __shared__ float rows[kGatherWarps][RW][M];
+  __shared__ __align__(16) float rows[kGatherWarps][RW][M];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_groups = b * (M / RW);
+  // rows of M >= 128 floats at a 16-byte aligned source: one 16-byte load per
+  // lane and 128 columns, fewer and larger reads over the CPU-GPU link
+  constexpr int PV = M / 128;
+  const bool vec = PV > 0 && (reinterpret_cast<uintptr_t>(d) & 15) == 0;
   for (int g = blockIdx.x * kGatherWarps + warp; g < n_groups; g += gridDim.x * kGatherWarps) {
     const int kk = g / (M / RW), er0 = (g % (M / RW)) * RW;
     const size_t k = (size_t)idx[kk];
-    float v[RW][PL];
+    if constexpr (PV > 0) {
+      if (vec) {
+        float4 v4[RW][PV];
 #pragma unroll
-    for (int r = 0; r < RW; ++r) {
-      const float* src = d + (k * M + storage_to_freq<M>(er0 + r)) * M;
+        for (int r = 0; r < RW; ++r) {
+          const float4* src = reinterpret_cast<const float4*>(d + (k * M + storage_to_freq<M>(er0 + r)) * M);
 #pragma unroll
-      for (int j = 0; j < PL; ++j)
-        if (lane + 32 * j < M) v[r][j] = src[lane + 32 * j];
+          for (int j = 0; j < PV; ++j) v4[r][j] = src[lane + 32 * j];
+        }
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+#pragma unroll
+          for (int j = 0; j < PV; ++j) *reinterpret_cast<float4*>(&rows[warp][r][4 * (lane + 32 * j)]) = v4[r][j];
+      }
     }
+    if (!vec) {
+      float v[RW][PL];
 #pragma unroll
-    for (int r = 0; r < RW; ++r)
+      for (int r = 0; r < RW; ++r) {
+        const float* src = d + (k * M + storage_to_freq<M>(er0 + r)) * M;
 #pragma unroll
-      for (int j = 0; j < PL; ++j)
-        if (lane + 32 * j < M) rows[warp][r][lane + 32 * j] = v[r][j];
+        for (int j = 0; j < PL; ++j)
+          if (lane + 32 * j < M) v[r][j] = src[lane + 32 * j];
+      }
+#pragma unroll
+      for (int r = 0; r < RW; ++r)
+#pragma unroll
+        for (int j = 0; j < PL; ++j)
+          if (lane + 32 * j < M) rows[warp][r][lane + 32 * j] = v[r][j];
+    }
     __syncwarp();
 #pragma unroll
     for (int r = 0; r < RW; ++r) {
