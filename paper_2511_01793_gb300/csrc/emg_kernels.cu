@@ -279,6 +279,34 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // ---------------------------------------------------------------------------
 // a_k in storage order: amp[k][e_r][e_c] = sqrt(max(d[k][f(e_r)][f(e_c)], 0)).
+// Warp-level max (sum) of v, written by lane 0 of each warp to sh[warp]; after
+// a barrier, partials_max / partials_sum combine them in warp order, as
+// block_max and block_sum_f do, so a caller can let one existing barrier serve.
+__device__ __forceinline__ void warp_partial_max(float v, float* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+}
+__device__ __forceinline__ void warp_partial_sum(float v, float* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+}
+template <int NT>
+__device__ __forceinline__ float partials_max(const float* sh) {
+  float r = sh[0];
+#pragma unroll
+  for (int i = 1; i < NT / 32; ++i) r = fmaxf(r, sh[i]);
+  return r;
+}
+template <int NT>
+__device__ __forceinline__ double partials_sum(const float* sh) {
+  double r = 0.0;
+#pragma unroll
+  for (int i = 0; i < NT / 32; ++i) r += (double)sh[i];
+  return r;
+}
+
 template <int M>
 __global__ void __launch_bounds__(256) k_amp_prep(const float* __restrict__ d, float* __restrict__ amp,
                                                   int n_pos) {
@@ -1035,7 +1063,9 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
       rowbuf[lr * SR + c] = cmul(a.probe[r * M + c], zk);
     mu_l = fmaxf(mu_l, cabs2(zk));
   }
-  const float mu_part = block_max<NT>(mu_l, redf);
+  // per-warp maxima of |z_k|^2; the barrier also orders the gather before the row passes
+  warp_partial_max(mu_l, redf);
+  __syncthreads();
   if constexpr (!RIN) {
     // a2: row passes on my rows
     gpass_a_fwd<M, H, SR, 1, NT>(rowbuf, tid);
@@ -1046,7 +1076,7 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
   cl.barrier_wait();  // all CTAs of the cluster resident
   // transpose 1: my rows x all storage columns -> column slabs
   if constexpr (!RIN) cluster_rows_to_cols<M, C>(cl, rank, rowbuf, colbuf, tid);
-  if (tid == 0) cluster_publish<C>(cl, rank, xf, mu_part);
+  if (tid == 0) cluster_publish<C>(cl, rank, xf, partials_max<NT>(redf));
   cl.sync();
   float mu = xf[0];
 #pragma unroll
@@ -1085,10 +1115,12 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_stepc(const StepArgs a) 
   }
   __syncthreads();
   gpass_a_inv<M, H, 1, SC, NT>(colbuf, tid);
-  const double phi_part = block_sum_f<NT>(acc, redf, redd);  // includes the barrier after the pass
+  // per-warp misfit partials; the barrier also orders the pass before the transpose
+  warp_partial_sum(acc, redf);
+  __syncthreads();
   // transpose 2: all rows x my columns -> row slabs
   cluster_cols_to_rows<M, C>(cl, rank, colbuf, rowbuf, tid);
-  if (tid == 0) cluster_publish<C>(cl, rank, xd, phi_part);
+  if (tid == 0) cluster_publish<C>(cl, rank, xd, partials_sum<NT>(redf));
   cl.sync();
   // a4: inverse row passes -> R (natural order) on my rows
   gpass_b<M, H, SR, 1, NT, true>(rowbuf, tid);
