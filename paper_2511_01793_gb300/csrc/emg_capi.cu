@@ -24,6 +24,9 @@ using emg::StepArgs;
 
 // Kernel kinds counted and timed by the profiling hooks.
 enum { kKindPrep = 0, kKindStep = 1, kKindApply = 2, kKindOther = 3, kKindDft = 4, kKinds = 5 };
+// Epochs whose misfit histories emg_reconstruct_host stages in the pinned scratch
+// (h_scalar holds 64 doubles: two histories and the wait flag).
+constexpr int kHostStageEpochs = 31;
 
 // A captured epoch and the state it was captured for.
 struct EpochGraph {
@@ -766,8 +769,11 @@ emg_status set_scatter_impl(emg_ctx* c, int32_t mode) {
 // `stream_src`: pinned host intensities that epoch 0 reads minibatch by
 // minibatch (graph path only; the amplitudes of all positions are in place
 // after it, since an epoch visits every position).
+// With `flag_out` (pinned host memory; FFT path only) the call does not wait:
+// it queues the copies of the misfit histories and of the bounded-wait flag
+// and leaves synchronising and checking the flag to the caller.
 emg_status run_epochs_impl(emg_ctx* c, int32_t n_epochs, const int32_t* order, double* running,
-                           double* misfit, const float* stream_src = nullptr) {
+                           double* misfit, const float* stream_src = nullptr, unsigned* flag_out = nullptr) {
   if (n_epochs < 0) return fail(c, EMG_EINVAL, "n_epochs < 0");
   if (n_epochs == 0) return EMG_OK;
   const int N = c->n_pos, B = c->par.minibatch;
@@ -833,6 +839,10 @@ emg_status run_epochs_impl(emg_ctx* c, int32_t n_epochs, const int32_t* order, d
   if (misfit)
     EMG_CUDA(c, cudaMemcpyAsync(misfit, c->d_hist + c->cap_hist, n_epochs * sizeof(double),
                                 cudaMemcpyDeviceToHost, c->stream));
+  if (flag_out && !c->tc) {
+    EMG_CUDA(c, cudaMemcpyAsync(flag_out, c->d_sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    return EMG_OK;
+  }
   if (running || misfit) {
     EMG_CUDA(c, cudaStreamSynchronize(c->stream));
     return check_tc_flag(c);
@@ -1262,13 +1272,29 @@ emg_status emg_reconstruct_host(emg_ctx* c, const float* intensity, float* objec
   float2* keep_p = c->probe;
   c->object = c->d_own_object;
   c->probe = c->d_own_probe;
-  st = run_epochs_impl(c, n_epochs, order, running_misfit, misfit, streamed);
+  // Everything is queued and waited for once: the misfit histories land in the
+  // context's pinned scratch when they fit (a copy to pageable memory would
+  // wait), and the bounded-wait flag is read there after the one wait.
+  const bool staged = !c->tc && n_epochs <= kHostStageEpochs;
+  double* h_run = staged && running_misfit ? c->h_scalar : running_misfit;
+  double* h_mis = staged && misfit ? c->h_scalar + kHostStageEpochs : misfit;
+  unsigned* h_flag = staged ? reinterpret_cast<unsigned*>(c->h_scalar + 2 * kHostStageEpochs) : nullptr;
+  if (h_flag) *h_flag = 0u;
+  st = run_epochs_impl(c, n_epochs, order, h_run, h_mis, streamed, h_flag);
   c->object = keep_o;
   c->probe = keep_p;
   if (st != EMG_OK) return st;
   EMG_CUDA(c, cudaMemcpyAsync(object, c->d_own_object, nz * sizeof(float2), cudaMemcpyDeviceToHost, c->stream));
   EMG_CUDA(c, cudaMemcpyAsync(probe, c->d_own_probe, nq * sizeof(float2), cudaMemcpyDeviceToHost, c->stream));
   EMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (staged) {
+    if (running_misfit) memcpy(running_misfit, h_run, (size_t)n_epochs * sizeof(double));
+    if (misfit) memcpy(misfit, h_mis, (size_t)n_epochs * sizeof(double));
+    if (*h_flag) {
+      EMG_CUDA(c, cudaMemset(c->d_sync + 2, 0, sizeof(unsigned)));
+      return fail(c, EMG_ETIMEOUT, "the step kernel's bounded wait for the fused probe prep gave up");
+    }
+  }
   return EMG_OK;
 }
 

@@ -315,6 +315,35 @@ def test_fused_probe_prep_equals_the_separate_kernel(lib, torch, m, levels, prol
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
+def test_host_buffer_call_reports_a_wait_that_gave_up_and_recovers(lib, torch):
+    """The host-buffer entry point queues its downloads and waits once; a bounded
+    wait that gave up in the step kernel (made to run out) still makes it return
+    EMG_ETIMEOUT, and the next call runs normally with the same result as a
+    fresh context."""
+    m = 128
+    case = Case(n=2 * m + 40, m=m, side=4, noise_peak=1e4, seed=97)
+    p = oracle_params(minibatch=10, levels=3, prolong="bilinear")
+    c = make_context(lib, case, p, seed=2)
+    d = np.ascontiguousarray(case.d, dtype=np.float32)
+    z = case.z0.astype(np.complex64).copy()
+    q = case.q0.astype(np.complex64).copy()
+    lib.emg_debug_prep_wait_extra(c.ctx, 1000)
+    with pytest.raises(lib.EmgError) as err:
+        lib.emg_reconstruct_host(c.ctx, d, z, q, 1, running=True)
+    assert err.value.status == lib.EMG_ETIMEOUT
+    lib.emg_debug_prep_wait_extra(c.ctx, 0)
+    z1, q1 = case.z0.astype(np.complex64).copy(), case.q0.astype(np.complex64).copy()
+    lib.emg_set_epoch(c.ctx, 0)
+    r1, _ = lib.emg_reconstruct_host(c.ctx, d, z1, q1, 2, running=True)
+    ref = make_context(lib, case, p, seed=2)
+    z2, q2 = case.z0.astype(np.complex64).copy(), case.q0.astype(np.complex64).copy()
+    r2, _ = lib.emg_reconstruct_host(ref.ctx, d, z2, q2, 2, running=True)
+    assert np.array_equal(z1, z2) and np.array_equal(q1, q2) and np.array_equal(r1, r2)
+    assert np.all(np.isfinite(r1)) and r1[0] > 0
+    c.close()
+    ref.close()
+
+
 def test_fused_prep_wait_gives_up_reports_and_recovers(lib, torch):
     """The step kernel's bounded wait for the fused prep, made to run out (it waits
     for prep tiles that never come): the call reports EMG_ETIMEOUT after about
