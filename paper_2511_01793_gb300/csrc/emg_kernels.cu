@@ -1924,12 +1924,14 @@ __global__ void __launch_bounds__(kApplyThreads, EMG_APPLY_MIN_BLOCKS) k_apply(c
     if (p0 < (int)mm) {
       for (int kb0 = g; kb0 < a.b; kb0 += 4 * kApplyProbeGroups) {
         float2 v[PP][4];
-        bool ok[4];
+        float mu[4];
+        // mu_k and Q~_k are loaded together; slots with mu_k = 0 are skipped when summing
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int kb = kb0 + u * kApplyProbeGroups;
-          ok[u] = kb < a.b && a.mu[kb] > 0.f;
-          if (ok[u]) {
+          mu[u] = 0.f;
+          if (kb < a.b) {
+            mu[u] = a.mu[kb];
             const float2* qrow = a.qt + (size_t)kb * mm + p0;
 #pragma unroll
             for (int h = 0; h < PP; ++h)
@@ -1938,7 +1940,7 @@ __global__ void __launch_bounds__(kApplyThreads, EMG_APPLY_MIN_BLOCKS) k_apply(c
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          if (ok[u]) {
+          if (mu[u] > 0.f) {
 #pragma unroll
             for (int h = 0; h < PP; ++h)
               if (p0 + 32 * h < (int)mm) s[h] = cadd(s[h], v[h][u]);
