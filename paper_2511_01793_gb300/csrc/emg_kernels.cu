@@ -2254,18 +2254,28 @@ cudaError_t launch_amp_prep(const float* d, float* amp, int m, int n_pos, cudaSt
   return cudaGetLastError();
 }
 
+// Shared memory each gather block reserves in all (its row buffer plus unused
+// dynamic shared memory, within the 48 KB a launch may ask for without opting
+// in).  At the bench size a block that large does not fit beside two step
+// CTAs, so the gathers run on the SMs the step leaves free instead of slowing
+// its CTAs: end to end 1.57M -> 1.62M positions/s (20 KB per block gave 1.44M).
+#ifndef EMG_GATHER_BLOCK_SMEM
+#define EMG_GATHER_BLOCK_SMEM (46 * 1024)
+#endif
 cudaError_t launch_amp_gather(const float* d, const int32_t* idx, int b, float* amp, int m, cudaStream_t s) {
   const int groups = b * (m / kGatherRows);
   int blocks = (groups + kGatherWarps - 1) / kGatherWarps;
   if (blocks > kGatherBlocks) blocks = kGatherBlocks;
   if (blocks == 0) return cudaSuccess;
   const dim3 th(kGatherWarps * 32);
+  const size_t rows_bytes = (size_t)kGatherWarps * kGatherRows * m * sizeof(float);
+  const size_t pad = rows_bytes < EMG_GATHER_BLOCK_SMEM ? EMG_GATHER_BLOCK_SMEM - rows_bytes : 0;
   switch (m) {
-    case 16: k_amp_gather<16><<<blocks, th, 0, s>>>(d, idx, b, amp); break;
-    case 32: k_amp_gather<32><<<blocks, th, 0, s>>>(d, idx, b, amp); break;
-    case 64: k_amp_gather<64><<<blocks, th, 0, s>>>(d, idx, b, amp); break;
-    case 128: k_amp_gather<128><<<blocks, th, 0, s>>>(d, idx, b, amp); break;
-    case 256: k_amp_gather<256><<<blocks, th, 0, s>>>(d, idx, b, amp); break;
+    case 16: k_amp_gather<16><<<blocks, th, pad, s>>>(d, idx, b, amp); break;
+    case 32: k_amp_gather<32><<<blocks, th, pad, s>>>(d, idx, b, amp); break;
+    case 64: k_amp_gather<64><<<blocks, th, pad, s>>>(d, idx, b, amp); break;
+    case 128: k_amp_gather<128><<<blocks, th, pad, s>>>(d, idx, b, amp); break;
+    case 256: k_amp_gather<256><<<blocks, th, pad, s>>>(d, idx, b, amp); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

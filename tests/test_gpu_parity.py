@@ -482,7 +482,7 @@ def test_deepest_hierarchy_and_single_position_at_the_largest_probe(lib, torch, 
     assert rel_err(z_g, z_o, mask) <= STEP_TOL and rel_err(q_g, q_o) <= STEP_TOL
 
 
-@pytest.mark.parametrize("m,levels", [(16, 1), (128, 3)])
+@pytest.mark.parametrize("m,levels", [(16, 1), (64, 2), (128, 3), (256, 3)])
 def test_pinned_host_intensity_equals_device_intensity(lib, torch, m, levels):
     """Pinned host data is read in place: all at once by emg_set_intensity, and
     minibatch by minibatch during the first epoch of the host-buffer entry point.
