@@ -1601,15 +1601,29 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_gradc(const GradArgs a) 
   float2* colbuf = sm + H * SR;
   float2* zbuf = colbuf + M * SC;
   __shared__ double xd[C];
-  __shared__ double redd[2];
   __shared__ float redf[NT / 32];
   const int tid = threadIdx.x;
   const int kb = blockIdx.x / C;
   const int k = a.first + kb;
   const int o_r = a.pos[2 * k], o_c = a.pos[2 * k + 1];
   const int row0 = rank * H;
+  constexpr int PER = TL::PER;
+  // amplitudes of my spectral slots: issued now, consumed after the row passes
+  float am_reg[SLOTS][N1];
+  {
+    const float* amp = a.amp + (size_t)k * M * M + rank * H;
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+      const int s = tid + t * NT, k2 = s / H, lc = s % H;
+#pragma unroll
+      for (int i = 0; i < N1; ++i) am_reg[t][i] = __ldg(amp + (i + N1 * k2) * M + lc);
+    }
+  }
   cluster_arrive_relaxed();
-  for (int p = tid; p < H * M; p += NT) {
+  // gather: the loads of 8 pixels of a thread in flight together
+#pragma unroll 8
+  for (int t = 0; t < PER; ++t) {
+    const int p = tid + t * NT;
     const int lr = p / M, c = p % M, r = row0 + lr;
     const float2 zk = gather_obj(a.object, a.n_rows, a.n_cols, o_r + r, o_c + c);
     zbuf[p] = zk;
@@ -1625,7 +1639,6 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_gradc(const GradArgs a) 
   cl.sync();
   gpass_a_fwd<M, H, 1, SC, NT>(colbuf, tid);
   __syncthreads();
-  const float* amp = a.amp + (size_t)k * M * M + rank * H;
   const float inv_m2 = 1.f / (float)(M * M);
   float acc = 0.f;
 #pragma unroll
@@ -1637,7 +1650,7 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_gradc(const GradArgs a) 
     Dft<N1, false>::run(v);
 #pragma unroll
     for (int i = 0; i < N1; ++i) {
-      const float am = amp[(i + N1 * k2) * M + lc];
+      const float am = am_reg[t][i];
       const float p2 = cabs2(v[i]);
       if (p2 > 0.f) {
         const float inv = rsqrtf(p2);
@@ -1655,9 +1668,11 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_gradc(const GradArgs a) 
   }
   __syncthreads();
   gpass_a_inv<M, H, 1, SC, NT>(colbuf, tid);
-  const double phi_part = block_sum_f<NT>(acc, redf, redd);
+  // per-warp misfit partials; the barrier also orders the pass before the transpose
+  warp_partial_sum(acc, redf);
+  __syncthreads();
   cluster_cols_to_rows<M, C>(cl, rank, colbuf, rowbuf, tid);
-  if (tid == 0) cluster_publish<C>(cl, rank, xd, phi_part);
+  if (tid == 0) cluster_publish<C>(cl, rank, xd, partials_sum<NT>(redf));
   cl.sync();
   gpass_b<M, H, SR, 1, NT, true>(rowbuf, tid);
   __syncthreads();
@@ -1665,13 +1680,26 @@ __global__ void __launch_bounds__(CTile<M, C>::NT, 1) k_gradc(const GradArgs a) 
   __syncthreads();
   float2* gz = a.gz + (size_t)kb * M * M;
   float2* gq = a.gq + (size_t)kb * M * M;
-  for (int p = tid; p < H * M; p += NT) {
-    const int lr = p / M, c = p % M, r = row0 + lr;
-    const float2 zk = zbuf[p];
-    const float2 q = a.probe[r * M + c];
-    const float2 e = csub(cmul(q, zk), rowbuf[lr * SR + c]);
-    gz[r * M + c] = cconjmul(q, e);
-    gq[r * M + c] = cconjmul(zk, e);
+  // patch gradients; the probe loads of 8 pixels of a thread are issued together
+  constexpr int UG = PER < 8 ? PER : 8;
+#pragma unroll 1
+  for (int t0 = 0; t0 < PER; t0 += UG) {
+    float2 qv[UG];
+#pragma unroll
+    for (int u = 0; u < UG; ++u) {
+      const int p = tid + (t0 + u) * NT;
+      qv[u] = __ldg(a.probe + (row0 + p / M) * M + p % M);
+    }
+#pragma unroll
+    for (int u = 0; u < UG; ++u) {
+      const int p = tid + (t0 + u) * NT;
+      const int lr = p / M, c = p % M, r = row0 + lr;
+      const float2 zk = zbuf[p];
+      const float2 q = qv[u];
+      const float2 e = csub(cmul(q, zk), rowbuf[lr * SR + c]);
+      gz[r * M + c] = cconjmul(q, e);
+      gq[r * M + c] = cconjmul(zk, e);
+    }
   }
   if (rank == 0 && tid == 0) {
     double tot = 0.0;
