@@ -274,7 +274,10 @@ emg_status emg_schedule_permutation(uint64_t seed, int64_t epoch, int32_t n, int
  * emg_set_intensity does, copies object (host complex64 [n_rows][n_cols]) and
  * probe (host complex64 [m][m]) to library-owned device buffers, runs
  * n_epochs as emg_run_epochs does and copies object and probe back.  The
- * context's bound device state is not touched.  Synchronises.
+ * context's bound device state is not touched.  Synchronises once: for up to
+ * 31 epochs the misfit histories and the flag of the step kernel's bounded
+ * wait come back through the context's pinned scratch beside the object and
+ * the probe; a wait that gave up returns EMG_ETIMEOUT after the copies.
  */
 emg_status emg_reconstruct_host(emg_ctx* ctx, const float* intensity, float* object,
                                 float* probe, int32_t n_epochs, const int32_t* order,
